@@ -1,0 +1,203 @@
+/*
+ * relearn.h -- C ABI of librelearn.so: the Barnes-Hut connectivity update of the
+ * Model of Structural Plasticity (MSP) on one GB300 (sm_103a).
+ *
+ * Paper: "I Like To Move It -- Computation Instead of Data in the Brain",
+ * arXiv 2509.26193. Sec. III-A defines the three sub-steps of a connectivity
+ * update (deletion, formation search, acceptance); Sec. III-B defines the
+ * octree, its bottom-up update and the Barnes-Hut partner search with restarts.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller unless marked
+ *     "host". The context owns all of its internal scratch (allocated once, in
+ *     relearn_create). Neuron ids are 0 .. n-1 in the caller's order.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     All work is enqueued on it; calls return before the GPU finishes unless a
+ *     host output (stats, get_*) is requested, which synchronises the stream.
+ *   - Argument and state errors are detected on the host and returned
+ *     immediately; nothing is enqueued then. Device-side conditions (capacity
+ *     overflow) are recorded in a device status word and returned by the next
+ *     synchronising call (relearn_last_error, relearn_get_*, or an update with
+ *     stats). The library never aborts the process and never traps the GPU.
+ *   - A context is bound to one device and is not thread-safe; calls on one
+ *     context must be issued from one host thread, on streams the caller keeps
+ *     ordered.
+ */
+#ifndef RELEARN_H
+#define RELEARN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RELEARN_OK = 0,
+    RELEARN_ERR_INVALID_ARG = 1, /* NULL where required, n out of range, sigma <= 0, theta < 0 */
+    RELEARN_ERR_CUDA = 2,        /* a CUDA runtime call failed; see relearn_last_error */
+    RELEARN_ERR_OOM = 3,         /* device allocation failed in relearn_create */
+    RELEARN_ERR_CAPACITY = 4,    /* searches or synapses exceeded the context's capacity */
+    RELEARN_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+    RELEARN_ERR_STATE = 6        /* call out of order (e.g. update before build) */
+} relearn_status;
+
+typedef struct relearn_ctx relearn_ctx;
+
+/* Parameters of one connectivity update or deletion pass.
+ *   sigma     kernel width (same length unit as the positions), > 0. The attraction of a
+ *             candidate node with `count` vacant dendritic elements at distance d is
+ *             count * exp(-d^2 / sigma^2).
+ *   theta     Barnes-Hut acceptance parameter, >= 0: a node is accepted when its cell
+ *             length (longest edge) divided by the distance to its centroid is < theta
+ *             (Sec. II; theta = 0 gives the exact O(n^2) draw).
+ *   seed      key of every Philox4x32-10 draw.
+ *   step      update index (< 2^32), part of every Philox counter.
+ *   flags     RELEARN_FLAG_* bits. */
+typedef struct {
+    float sigma;
+    float theta;
+    uint64_t seed;
+    uint64_t step;
+    uint32_t flags;
+    uint32_t reserved;
+} relearn_params;
+
+/* Record per-search diagnostics (root-frontier ln S, node evaluations, restarts),
+ * readable with relearn_get_search_diag. Costs a little extra memory traffic. */
+#define RELEARN_FLAG_DIAG 1u
+
+/* Host-side summary of one update (filled when a stats pointer is passed; this
+ * synchronises the stream). Times are CUDA-event milliseconds. */
+typedef struct {
+    int64_t searches;          /* Q = sum of vacant axonal elements at the start */
+    int64_t failed;            /* searches with zero total attraction */
+    int64_t requests_declined; /* requests refused by over-requested targets */
+    int64_t formed;            /* synapses formed */
+    int64_t synapses;          /* synapses stored after the update */
+    float ms_reduce, ms_search, ms_accept, ms_apply, ms_total;
+} relearn_update_stats;
+
+/* Create a context on CUDA device `device` that can hold up to max_neurons
+ * neurons, max_synapses synapses and max_searches searches per update
+ * (0 = 8 * max_neurons). Allocates all device scratch now.
+ * Returns RELEARN_ERR_OOM if the allocation fails (nothing is leaked). */
+relearn_status relearn_create(relearn_ctx **out, int device, int64_t max_neurons,
+                              int64_t max_synapses, int64_t max_searches);
+
+/* Free the context and all of its device memory (synchronises the device). NULL is ok. */
+relearn_status relearn_destroy(relearn_ctx *ctx);
+
+/* Build the spatial octree over n neurons (Sec. III-B "Spatial octree").
+ *   x, y, z     device float[n], positions (SoA). Copied into the context in
+ *               Morton order; the caller may free them afterwards.
+ *   vac_de      device int32[n] or NULL: when given, the bottom-up update also runs, so
+ *               the tree is ready for inspection (relearn_get_tree).
+ *   box_lo3/hi3 host float[3] each, or both NULL: the domain box. NULL = the bounding box
+ *               of the positions. Positions outside a given box are clamped to it.
+ * Steps: 30-bit Morton codes (10 bits per axis, FP32 quantisation
+ * floor(((x - lo) * (1/(hi - lo))) * 1024) clamped to 0..1023), a stable radix sort of
+ * (code, id), and the compressed octree: the root, every cell with >= 2 non-empty
+ * children, every depth-10 cell with >= 2 neurons (a bucket) and one leaf per neuron, in
+ * pre-order with skip links. The topology stays valid until the next build.
+ * Errors: INVALID_ARG for n < 1, n > max_neurons, NULL positions. */
+relearn_status relearn_build_octree(relearn_ctx *ctx, int64_t n, const float *x, const float *y,
+                                    const float *z, const int32_t *vac_de, const float *box_lo3,
+                                    const float *box_hi3, void *stream);
+
+/* One connectivity update (Sec. III-A "Update of synapses", formation sub-phase, with the
+ * Barnes-Hut search of Sec. III-B):
+ *   1. bottom-up update of the octree from vac_de (counts, count-weighted centroids);
+ *   2. one search per vacant axonal element (neuron i, element e < vac_ax[i]) from the
+ *      root: rejected nodes are replaced by their children, one accepted node is drawn
+ *      with probability proportional to its attraction (draw word
+ *      Philox4x32-10({i, step, (e << 8) | depth(start), 0}, seed).x), an inner node
+ *      restarts the search from itself, a leaf becomes the request target; the searching
+ *      neuron's own leaf has attraction 0; zero total attraction = failed search;
+ *   3. acceptance: a target with more requests than vac_de accepts the vac_de requests with
+ *      the smallest priority Philox4x32-10({i, step, (e << 8) | 0xFF, 1}, seed).x
+ *      (ties by source id, then element);
+ *   4. apply: accepted requests decrement vac_ax[src] and vac_de[tgt] and add synapse
+ *      (src, tgt, sign = type[src] ? -1 : +1) to the context's store.
+ *   params    host pointer.
+ *   vac_ax    device int32[n], in/out.  vac_de  device int32[n], in/out (negative = 0).
+ *   type      device uint8[n]: 0 excitatory, 1 inhibitory.
+ *   stats     host pointer or NULL; non-NULL synchronises the stream and fills it.
+ * Errors: STATE before a build; INVALID_ARG for bad params or NULL arrays; CAPACITY
+ * (device status) if Q > max_searches or the store would overflow -- then nothing is
+ * applied. */
+relearn_status relearn_update_connectivity(relearn_ctx *ctx, const relearn_params *params,
+                                           int32_t *vac_ax, int32_t *vac_de,
+                                           const uint8_t *type, relearn_update_stats *stats,
+                                           void *stream);
+
+/* Deletion pass (Sec. III-A "Update of synapses", first sub-phase).
+ *   retract_ax, retract_de  device int32[n] (>= 0): elements each neuron retracts.
+ *   vac_ax, vac_de          device int32[n], in/out.
+ * Vacant elements are retracted first. The remainder (capped by the neuron's bound
+ * elements) breaks that many of its synapses on the same side, chosen by the smallest
+ * priority Philox4x32-10({neuron, step, slot, 2 (axonal) | 3 (dendritic)}, seed).x over the
+ * slots of its out-row (ordered by target) or in-row (ordered by source); ties by slot. A
+ * broken synapse gives its partner one vacant element, unless both ends picked it.
+ * If `broken` (host) is non-NULL the stream is synchronised and the count written. */
+relearn_status relearn_delete_synapses(relearn_ctx *ctx, const relearn_params *params,
+                                       const int32_t *retract_ax, const int32_t *retract_de,
+                                       int32_t *vac_ax, int32_t *vac_de, int64_t *broken,
+                                       void *stream);
+
+/* Spike delivery over the synapse store (Sec. III-A "Update of electrical activity"):
+ *   input[t] = sum over synapses s -> t of sign(s) * spiked[s]   (duplicates count).
+ *   spiked  device uint8[n] (0/1).  input  device int32[n], written. */
+relearn_status relearn_deliver_spikes(relearn_ctx *ctx, const uint8_t *spiked, int32_t *input,
+                                      void *stream);
+
+/* Copy the synapse store to host arrays in canonical order (by source, then target).
+ * `count` (host) receives the number stored; src/tgt/sign may be NULL to query only the
+ * count, else they must hold `capacity` entries (INVALID_ARG if too small).
+ * Synchronises the context's stream and returns any pending device status. */
+relearn_status relearn_get_synapses(relearn_ctx *ctx, int64_t capacity, int64_t *count,
+                                    int32_t *src, int32_t *tgt, int8_t *sign);
+
+/* Replace the synapse store from host arrays (any order; it is canonicalised).
+ * Used for checkpoint/resume together with the vacancy arrays. Synchronous. */
+relearn_status relearn_set_synapses(relearn_ctx *ctx, int64_t count, const int32_t *src,
+                                    const int32_t *tgt, const int8_t *sign);
+
+/* Copy the last update's requests to host arrays, in canonical query order (neuron id,
+ * then element): tgt (-1 = failed search) and accept (0/1). `count` receives Q.
+ * Synchronous. */
+relearn_status relearn_get_requests(relearn_ctx *ctx, int64_t capacity, int64_t *count,
+                                    int32_t *tgt, uint8_t *accept);
+
+/* Per-search diagnostics of the last update run with RELEARN_FLAG_DIAG, canonical query
+ * order: ln_s0 (natural log of the root frontier's total attraction, -inf when zero),
+ * evals (node evaluations with count > 0 over all draws), restarts. Synchronous. */
+relearn_status relearn_get_search_diag(relearn_ctx *ctx, int64_t capacity, int64_t *count,
+                                       double *ln_s0, int32_t *evals, int32_t *restarts);
+
+/* Copy the current octree to host arrays, pre-order (parent first, children in Morton
+ * order). Per node: depth (0..10; leaves report the depth of their parent + 1, capped at
+ * 11 inside buckets), first (position of its first neuron in Morton order), size (neurons),
+ * is_leaf, neuron (id for leaves, -1 otherwise), count (vacant dendritic elements) and
+ * centroid cx/cy/cz (float, 0 when count == 0). Any output may be NULL. `perm` (host
+ * int32[n] or NULL) receives the neuron ids in Morton order. Synchronous. */
+relearn_status relearn_get_tree(relearn_ctx *ctx, int64_t capacity, int64_t *num_nodes,
+                                int32_t *depth, int32_t *first, int32_t *size, int32_t *is_leaf,
+                                int32_t *neuron, int32_t *count, float *cx, float *cy, float *cz,
+                                int32_t *perm);
+
+/* Device Philox4x32-10 over `count` blocks (the generator the kernels use): ctr is
+ * device uint32[4*count], key device uint32[2*count], out device uint32[4*count]. */
+relearn_status relearn_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out,
+                                     int64_t count, void *stream);
+
+/* Synchronise the context's last stream, fold the device status word into the result and
+ * return it; *msg (host, may be NULL) points at a static description of the last error.
+ * Clears the stored error. */
+relearn_status relearn_last_error(relearn_ctx *ctx, const char **msg);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RELEARN_H */

@@ -1,0 +1,539 @@
+// C ABI of librelearn (declared in include/relearn.h): argument checks,
+// context allocation, and the order of the kernels of each call.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace rl;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+relearn_status fail(relearn_ctx *c, relearn_status s, const char *what)
+{
+    if (c) {
+        c->host_error = s;
+        snprintf(c->msg, sizeof(c->msg), "%s", what);
+    }
+    return s;
+}
+
+relearn_status cuda_fail(relearn_ctx *c, cudaError_t e, const char *where)
+{
+    if (c) {
+        c->host_error = RELEARN_ERR_CUDA;
+        snprintf(c->msg, sizeof(c->msg), "%s: %s", where, cudaGetErrorString(e));
+    }
+    return RELEARN_ERR_CUDA;
+}
+
+#define CK(call, where)                                                                           \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where);                                    \
+    } while (0)
+
+template <typename T>
+cudaError_t alloc(T **p, int64_t count, std::vector<void *> &owned)
+{
+    size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e == cudaSuccess) owned.push_back((void *)*p);
+    return e;
+}
+
+void free_all(relearn_ctx *c)
+{
+    void **ptrs[] = {
+        (void **)&c->d_status,   (void **)&c->d_i64,        (void **)&c->d_i32,
+        (void **)&c->d_geom,     (void **)&c->d_sc,         (void **)&c->d_codes,
+        (void **)&c->d_codes_alt, (void **)&c->d_perm,      (void **)&c->d_perm_alt,
+        (void **)&c->d_pos,      (void **)&c->d_mask,       (void **)&c->d_base,
+        (void **)&c->d_nodes,    (void **)&c->d_parent,     (void **)&c->d_nchild,
+        (void **)&c->d_leaf,     (void **)&c->d_acc,        (void **)&c->d_arrive,
+        (void **)&c->d_cnt,      (void **)&c->d_qoff_s,     (void **)&c->d_qoff_o,
+        (void **)&c->d_qsrc,     (void **)&c->d_req_src,    (void **)&c->d_req_elem,
+        (void **)&c->d_req_tgt,  (void **)&c->d_req_acc,    (void **)&c->d_req_prio,
+        (void **)&c->d_bucket,   (void **)&c->d_tcnt,       (void **)&c->d_toff,
+        (void **)&c->d_tfill,    (void **)&c->d_newpos,     (void **)&c->d_diag_lns,
+        (void **)&c->d_diag_evals, (void **)&c->d_diag_restarts, (void **)&c->d_syn_src,
+        (void **)&c->d_syn_tgt,  (void **)&c->d_syn_sign,   (void **)&c->d_key,
+        (void **)&c->d_key_alt,  (void **)&c->d_val,        (void **)&c->d_val_alt,
+        (void **)&c->d_key32,    (void **)&c->d_key32_alt,  (void **)&c->d_out_ptr,
+        (void **)&c->d_in_ptr,   (void **)&c->d_in_src,     (void **)&c->d_in_syn,
+        (void **)&c->d_in_sign,  (void **)&c->d_prio_ax,    (void **)&c->d_prio_de,
+        (void **)&c->d_sel_ax,   (void **)&c->d_sel_de,     (void **)&c->d_need_ax,
+        (void **)&c->d_need_de,  (void **)&c->d_keep,       (void **)&c->scan.block_sums,
+        (void **)&c->sort.hist};
+    for (void **p : ptrs) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+    c->sort.scan.block_sums = nullptr;
+    for (cudaEvent_t &ev : c->ev)
+        if (ev) {
+            cudaEventDestroy(ev);
+            ev = nullptr;
+        }
+}
+
+bool params_ok(const relearn_params *p)
+{
+    return p && p->sigma > 0.0f && p->sigma < 3.0e38f && p->theta >= 0.0f &&
+           p->theta < 3.0e38f && p->step <= 0xffffffffull;
+}
+
+relearn_status read_status(relearn_ctx *c)
+{
+    int32_t st = 0;
+    cudaError_t e = cudaMemcpy(&st, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading device status");
+    if (st != 0) {
+        cudaMemset(c->d_status, 0, sizeof(int32_t));
+        return fail(c, (relearn_status)st,
+                    st == RELEARN_ERR_CAPACITY ? "capacity exceeded on the device (searches or "
+                                                 "synapses); nothing was applied"
+                                               : "device-side error");
+    }
+    return RELEARN_OK;
+}
+
+relearn_status sync(relearn_ctx *c)
+{
+    cudaError_t e = cudaStreamSynchronize(c->last_stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    return read_status(c);
+}
+
+} // namespace
+
+extern "C" {
+
+relearn_status relearn_create(relearn_ctx **out, int device, int64_t max_neurons,
+                              int64_t max_synapses, int64_t max_searches)
+{
+    if (!out) return RELEARN_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (max_neurons < 1 || max_neurons > (int64_t)0x3fffffff || max_synapses < 1 ||
+        max_synapses > (int64_t)0x7ffffff0 || max_searches < 0 ||
+        max_searches > (int64_t)0x7ffffff0)
+        return RELEARN_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return RELEARN_ERR_INVALID_ARG;
+    DeviceGuard g(device);
+    if (!g.ok) return RELEARN_ERR_CUDA;
+    relearn_ctx *c = new (std::nothrow) relearn_ctx();
+    if (!c) return RELEARN_ERR_OOM;
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (c->num_sms < 1) c->num_sms = 1;
+    c->max_neurons = max_neurons;
+    c->max_synapses = max_synapses;
+    c->max_searches = max_searches ? max_searches : std::min<int64_t>(8 * max_neurons, 0x7ffffff0);
+    c->max_nodes = 2 * max_neurons + 1;
+    const int64_t N = max_neurons, S = max_synapses, QC = c->max_searches, M = c->max_nodes;
+    std::vector<void *> owned;
+    cudaError_t e = cudaSuccess;
+#define A(ptr, cnt)                                                                               \
+    if (e == cudaSuccess) e = alloc(&c->ptr, (cnt), owned)
+    A(d_status, 1);
+    A(d_i64, 16);
+    A(d_i32, 16);
+    A(d_geom, 1);
+    A(d_sc, 1);
+    A(d_codes, N);
+    A(d_codes_alt, N);
+    A(d_perm, N);
+    A(d_perm_alt, N);
+    A(d_pos, N);
+    A(d_mask, N);
+    A(d_base, N + 1);
+    A(d_nodes, M);
+    A(d_parent, M);
+    A(d_nchild, M);
+    A(d_leaf, N);
+    A(d_acc, 4 * M);
+    A(d_arrive, M);
+    A(d_cnt, N + 1);
+    A(d_qoff_s, N + 1);
+    A(d_qoff_o, N + 1);
+    A(d_qsrc, QC);
+    A(d_req_src, QC);
+    A(d_req_elem, QC);
+    A(d_req_tgt, QC);
+    A(d_req_acc, QC);
+    A(d_req_prio, QC);
+    A(d_bucket, QC);
+    A(d_tcnt, N + 1);
+    A(d_toff, N + 1);
+    A(d_tfill, N + 1);
+    A(d_newpos, QC + 1);
+    A(d_diag_lns, QC);
+    A(d_diag_evals, QC);
+    A(d_diag_restarts, QC);
+    A(d_syn_src, S);
+    A(d_syn_tgt, S);
+    A(d_syn_sign, S);
+    A(d_key, S);
+    A(d_key_alt, S);
+    A(d_val, std::max(S, N));
+    A(d_val_alt, std::max(S, N));
+    A(d_key32, S);
+    A(d_key32_alt, S);
+    A(d_out_ptr, N + 1);
+    A(d_in_ptr, N + 1);
+    A(d_in_src, S);
+    A(d_in_syn, S);
+    A(d_in_sign, S);
+    A(d_prio_ax, S);
+    A(d_prio_de, S);
+    A(d_sel_ax, S);
+    A(d_sel_de, S);
+    A(d_need_ax, N);
+    A(d_need_de, N);
+    A(d_keep, S + 1);
+    const int64_t sort_blocks = sort_blocks_needed(std::max(N, S));
+    A(sort.hist, 256 * sort_blocks);
+    int64_t scan_blocks = std::max({scan_blocks_needed(N + 1), scan_blocks_needed(QC),
+                                    scan_blocks_needed(S), scan_blocks_needed(256 * sort_blocks)});
+    A(scan.block_sums, scan_blocks + 1);
+#undef A
+    if (e == cudaSuccess) {
+        c->scan.max_blocks = scan_blocks;
+        c->sort.max_blocks = sort_blocks;
+        c->sort.scan = c->scan;
+        for (cudaEvent_t &ev : c->ev)
+            if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    }
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->d_i64, 0, 16 * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMemset(c->d_i32, 0, 16 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        relearn_status s = (e == cudaErrorMemoryAllocation) ? RELEARN_ERR_OOM : RELEARN_ERR_CUDA;
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return s;
+    }
+    *out = c;
+    return RELEARN_OK;
+}
+
+relearn_status relearn_destroy(relearn_ctx *c)
+{
+    if (!c) return RELEARN_OK;
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+    return RELEARN_OK;
+}
+
+relearn_status relearn_build_octree(relearn_ctx *c, int64_t n, const float *x, const float *y,
+                                    const float *z, const int32_t *vac_de, const float *box_lo3,
+                                    const float *box_hi3, void *stream)
+{
+    if (!c) return RELEARN_ERR_INVALID_ARG;
+    if (n < 1 || n > c->max_neurons)
+        return fail(c, RELEARN_ERR_INVALID_ARG, "build_octree: n out of range");
+    if (!x || !y || !z) return fail(c, RELEARN_ERR_INVALID_ARG, "build_octree: NULL position");
+    if ((box_lo3 == nullptr) != (box_hi3 == nullptr))
+        return fail(c, RELEARN_ERR_INVALID_ARG, "build_octree: give both box corners or none");
+    if (box_lo3)
+        for (int a = 0; a < 3; ++a)
+            if (!(box_hi3[a] >= box_lo3[a]))
+                return fail(c, RELEARN_ERR_INVALID_ARG, "build_octree: box_hi < box_lo");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(c, RELEARN_ERR_CUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    const bool reset_store = !c->built || n != c->n;
+    c->n = n;
+    CK(octree_build(c, n, x, y, z, box_lo3, box_hi3, st), "octree build");
+    if (vac_de) CK(octree_reduce(c, vac_de, st), "octree reduce");
+    if (reset_store) {
+        CK(cudaMemsetAsync(c->d_i32 + I32_NSYN, 0, sizeof(int32_t), st), "store reset");
+        CK(cudaMemsetAsync(c->d_i64 + I64_NSYN, 0, sizeof(int64_t), st), "store reset");
+        CK(rebuild_views(c, st), "views");
+    }
+    c->built = true;
+    c->diag_valid = false;
+    return RELEARN_OK;
+}
+
+relearn_status relearn_update_connectivity(relearn_ctx *c, const relearn_params *p,
+                                           int32_t *vac_ax, int32_t *vac_de,
+                                           const uint8_t *type, relearn_update_stats *stats,
+                                           void *stream)
+{
+    if (!c) return RELEARN_ERR_INVALID_ARG;
+    if (!c->built) return fail(c, RELEARN_ERR_STATE, "update before build_octree");
+    if (!params_ok(p)) return fail(c, RELEARN_ERR_INVALID_ARG, "update: bad params");
+    if (!vac_ax || !vac_de || !type)
+        return fail(c, RELEARN_ERR_INVALID_ARG, "update: NULL array");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(c, RELEARN_ERR_CUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    if (stats) CK(cudaEventRecord(c->ev[0], st), "event");
+    CK(octree_reduce(c, vac_de, st), "reduce");
+    if (stats) CK(cudaEventRecord(c->ev[1], st), "event");
+    CK(search_prepare(c, *p, vac_ax, st), "search prepare");
+    CK(search_run(c, *p, st), "search");
+    if (stats) CK(cudaEventRecord(c->ev[2], st), "event");
+    CK(accept_requests(c, *p, vac_de, st), "accept");
+    if (stats) CK(cudaEventRecord(c->ev[3], st), "event");
+    CK(apply_requests(c, vac_ax, vac_de, type, st), "apply");
+    if (stats) CK(cudaEventRecord(c->ev[4], st), "event");
+    c->diag_valid = (p->flags & RELEARN_FLAG_DIAG) != 0;
+    if (stats) {
+        relearn_status s = sync(c);
+        int64_t h[16];
+        CK(cudaMemcpy(h, c->d_i64, sizeof(h), cudaMemcpyDeviceToHost), "stats copy");
+        memset(stats, 0, sizeof(*stats));
+        stats->searches = h[I64_Q];
+        stats->failed = h[I64_FAILED];
+        stats->requests_declined = h[I64_DECLINED];
+        stats->formed = h[I64_FORMED];
+        stats->synapses = h[I64_NSYN];
+        cudaEventElapsedTime(&stats->ms_reduce, c->ev[0], c->ev[1]);
+        cudaEventElapsedTime(&stats->ms_search, c->ev[1], c->ev[2]);
+        cudaEventElapsedTime(&stats->ms_accept, c->ev[2], c->ev[3]);
+        cudaEventElapsedTime(&stats->ms_apply, c->ev[3], c->ev[4]);
+        cudaEventElapsedTime(&stats->ms_total, c->ev[0], c->ev[4]);
+        return s;
+    }
+    return RELEARN_OK;
+}
+
+relearn_status relearn_delete_synapses(relearn_ctx *c, const relearn_params *p,
+                                       const int32_t *retract_ax, const int32_t *retract_de,
+                                       int32_t *vac_ax, int32_t *vac_de, int64_t *broken,
+                                       void *stream)
+{
+    if (!c) return RELEARN_ERR_INVALID_ARG;
+    if (!c->built) return fail(c, RELEARN_ERR_STATE, "delete before build_octree");
+    if (!p || p->step > 0xffffffffull) return fail(c, RELEARN_ERR_INVALID_ARG, "delete: params");
+    if (!retract_ax || !retract_de || !vac_ax || !vac_de)
+        return fail(c, RELEARN_ERR_INVALID_ARG, "delete: NULL array");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(c, RELEARN_ERR_CUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    CK(delete_synapses(c, *p, retract_ax, retract_de, vac_ax, vac_de, st), "delete");
+    if (broken) {
+        relearn_status s = sync(c);
+        CK(cudaMemcpy(broken, c->d_i64 + I64_BROKEN, sizeof(int64_t), cudaMemcpyDeviceToHost),
+           "copy");
+        return s;
+    }
+    return RELEARN_OK;
+}
+
+relearn_status relearn_deliver_spikes(relearn_ctx *c, const uint8_t *spiked, int32_t *input,
+                                      void *stream)
+{
+    if (!c) return RELEARN_ERR_INVALID_ARG;
+    if (!c->built) return fail(c, RELEARN_ERR_STATE, "deliver_spikes before build_octree");
+    if (!spiked || !input) return fail(c, RELEARN_ERR_INVALID_ARG, "deliver_spikes: NULL array");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(c, RELEARN_ERR_CUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    CK(deliver_spikes(c, spiked, input, st), "deliver spikes");
+    return RELEARN_OK;
+}
+
+relearn_status relearn_get_synapses(relearn_ctx *c, int64_t capacity, int64_t *count,
+                                    int32_t *src, int32_t *tgt, int8_t *sign)
+{
+    if (!c || !count) return RELEARN_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    relearn_status s = sync(c);
+    int32_t m = 0;
+    CK(cudaMemcpy(&m, c->d_i32 + I32_NSYN, sizeof(int32_t), cudaMemcpyDeviceToHost), "copy");
+    *count = m;
+    if (src || tgt || sign) {
+        if (capacity < m) return fail(c, RELEARN_ERR_INVALID_ARG, "get_synapses: capacity");
+        if (src) CK(cudaMemcpy(src, c->d_syn_src, m * 4, cudaMemcpyDeviceToHost), "copy");
+        if (tgt) CK(cudaMemcpy(tgt, c->d_syn_tgt, m * 4, cudaMemcpyDeviceToHost), "copy");
+        if (sign) CK(cudaMemcpy(sign, c->d_syn_sign, m, cudaMemcpyDeviceToHost), "copy");
+    }
+    return s;
+}
+
+relearn_status relearn_set_synapses(relearn_ctx *c, int64_t count, const int32_t *src,
+                                    const int32_t *tgt, const int8_t *sign)
+{
+    if (!c) return RELEARN_ERR_INVALID_ARG;
+    if (!c->built) return fail(c, RELEARN_ERR_STATE, "set_synapses before build_octree");
+    if (count < 0 || count > c->max_synapses)
+        return fail(c, RELEARN_ERR_INVALID_ARG, "set_synapses: count out of range");
+    if (count > 0 && (!src || !tgt || !sign))
+        return fail(c, RELEARN_ERR_INVALID_ARG, "set_synapses: NULL array");
+    for (int64_t k = 0; k < count; ++k)
+        if (src[k] < 0 || src[k] >= c->n || tgt[k] < 0 || tgt[k] >= c->n ||
+            (sign[k] != 1 && sign[k] != -1))
+            return fail(c, RELEARN_ERR_INVALID_ARG, "set_synapses: id or sign out of range");
+    DeviceGuard g(c->device);
+    relearn_status s0 = sync(c);
+    if (s0 != RELEARN_OK) return s0;
+    cudaStream_t st = c->last_stream;
+    if (count > 0) {
+        CK(cudaMemcpy(c->d_syn_src, src, count * 4, cudaMemcpyHostToDevice), "copy");
+        CK(cudaMemcpy(c->d_syn_tgt, tgt, count * 4, cudaMemcpyHostToDevice), "copy");
+        CK(cudaMemcpy(c->d_syn_sign, sign, count, cudaMemcpyHostToDevice), "copy");
+    }
+    int32_t m = (int32_t)count;
+    int64_t m64 = count;
+    CK(cudaMemcpy(c->d_i32 + I32_NSYN, &m, sizeof(m), cudaMemcpyHostToDevice), "copy");
+    CK(cudaMemcpy(c->d_i64 + I64_NSYN, &m64, sizeof(m64), cudaMemcpyHostToDevice), "copy");
+    CK(canonicalise_store(c, st), "canonicalise");
+    return sync(c);
+}
+
+relearn_status relearn_get_requests(relearn_ctx *c, int64_t capacity, int64_t *count,
+                                    int32_t *tgt, uint8_t *accept)
+{
+    if (!c || !count) return RELEARN_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    relearn_status s = sync(c);
+    int32_t q = 0;
+    CK(cudaMemcpy(&q, c->d_i32 + I32_Q, sizeof(int32_t), cudaMemcpyDeviceToHost), "copy");
+    *count = q;
+    if (tgt || accept) {
+        if (capacity < q) return fail(c, RELEARN_ERR_INVALID_ARG, "get_requests: capacity");
+        if (tgt) CK(cudaMemcpy(tgt, c->d_req_tgt, (size_t)q * 4, cudaMemcpyDeviceToHost), "copy");
+        if (accept)
+            CK(cudaMemcpy(accept, c->d_req_acc, (size_t)q, cudaMemcpyDeviceToHost), "copy");
+    }
+    return s;
+}
+
+relearn_status relearn_get_search_diag(relearn_ctx *c, int64_t capacity, int64_t *count,
+                                       double *ln_s0, int32_t *evals, int32_t *restarts)
+{
+    if (!c || !count) return RELEARN_ERR_INVALID_ARG;
+    if (!c->diag_valid) return fail(c, RELEARN_ERR_STATE, "no update ran with RELEARN_FLAG_DIAG");
+    DeviceGuard g(c->device);
+    relearn_status s = sync(c);
+    int32_t q = 0;
+    CK(cudaMemcpy(&q, c->d_i32 + I32_Q, sizeof(int32_t), cudaMemcpyDeviceToHost), "copy");
+    *count = q;
+    if (ln_s0 || evals || restarts) {
+        if (capacity < q) return fail(c, RELEARN_ERR_INVALID_ARG, "get_search_diag: capacity");
+        if (ln_s0) CK(cudaMemcpy(ln_s0, c->d_diag_lns, (size_t)q * 8, cudaMemcpyDeviceToHost), "copy");
+        if (evals) CK(cudaMemcpy(evals, c->d_diag_evals, (size_t)q * 4, cudaMemcpyDeviceToHost), "copy");
+        if (restarts)
+            CK(cudaMemcpy(restarts, c->d_diag_restarts, (size_t)q * 4, cudaMemcpyDeviceToHost),
+               "copy");
+    }
+    return s;
+}
+
+relearn_status relearn_get_tree(relearn_ctx *c, int64_t capacity, int64_t *num_nodes,
+                                int32_t *depth, int32_t *first, int32_t *size, int32_t *is_leaf,
+                                int32_t *neuron, int32_t *count, float *cx, float *cy, float *cz,
+                                int32_t *perm)
+{
+    if (!c || !num_nodes) return RELEARN_ERR_INVALID_ARG;
+    if (!c->built) return fail(c, RELEARN_ERR_STATE, "get_tree before build_octree");
+    DeviceGuard g(c->device);
+    relearn_status s = sync(c);
+    int64_t m = 0;
+    CK(cudaMemcpy(&m, c->d_i64 + I64_NODES, sizeof(m), cudaMemcpyDeviceToHost), "copy");
+    *num_nodes = m;
+    const int64_t n = c->n;
+    std::vector<int32_t> hp;
+    if (perm || neuron) {
+        hp.resize(n);
+        CK(cudaMemcpy(hp.data(), c->d_perm, n * 4, cudaMemcpyDeviceToHost), "copy");
+        if (perm) memcpy(perm, hp.data(), n * 4);
+    }
+    if (depth || first || size || is_leaf || neuron || count || cx || cy || cz) {
+        if (capacity < m) return fail(c, RELEARN_ERR_INVALID_ARG, "get_tree: capacity");
+        std::vector<Node> h(m);
+        CK(cudaMemcpy(h.data(), c->d_nodes, m * sizeof(Node), cudaMemcpyDeviceToHost), "copy");
+        for (int64_t v = 0; v < m; ++v) {
+            const Node &nd = h[v];
+            const bool leaf = (nd.t.meta & kLeafBit) != 0;
+            const int32_t f = nd.t.neuron;
+            const int32_t fe = nd.t.escape < m ? h[nd.t.escape].t.neuron : (int32_t)n;
+            if (depth) depth[v] = nd.t.meta & 15;
+            if (first) first[v] = f;
+            if (size) size[v] = leaf ? 1 : fe - f;
+            if (is_leaf) is_leaf[v] = leaf;
+            if (neuron) neuron[v] = leaf ? hp[f] : -1;
+            if (count) count[v] = nd.t.icount;
+            if (cx) cx[v] = nd.g.cx;
+            if (cy) cy[v] = nd.g.cy;
+            if (cz) cz[v] = nd.g.cz;
+        }
+    }
+    return s;
+}
+
+} // extern "C"
+
+namespace {
+__global__ void philox_kernel(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint4 r = philox4x32_10(make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]),
+                                make_uint2(key[2 * i], key[2 * i + 1]));
+        out[4 * i] = r.x;
+        out[4 * i + 1] = r.y;
+        out[4 * i + 2] = r.z;
+        out[4 * i + 3] = r.w;
+    }
+}
+} // namespace
+
+extern "C" {
+
+relearn_status relearn_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out,
+                                     int64_t count, void *stream)
+{
+    if (count < 0 || (count > 0 && (!ctr || !key || !out))) return RELEARN_ERR_INVALID_ARG;
+    if (count == 0) return RELEARN_OK;
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    philox_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(ctr, key, out, count);
+    return cudaGetLastError() == cudaSuccess ? RELEARN_OK : RELEARN_ERR_CUDA;
+}
+
+relearn_status relearn_last_error(relearn_ctx *c, const char **msg)
+{
+    if (!c) {
+        if (msg) *msg = "NULL context";
+        return RELEARN_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(c->device);
+    relearn_status s = sync(c);
+    if (s == RELEARN_OK) s = c->host_error;
+    if (msg) *msg = s == RELEARN_OK ? "" : c->msg;
+    c->host_error = RELEARN_OK;
+    return s;
+}
+
+} // extern "C"

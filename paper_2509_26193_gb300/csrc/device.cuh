@@ -1,0 +1,75 @@
+// Device-side helpers shared by the library's kernels (not by the oracle).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rl {
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 multiplies
+// with the Weyl key schedule. Written from the published definition.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t lo0 = m0 * c.x, hi0 = __umulhi(m0, c.x);
+        uint32_t lo1 = m1 * c.z, hi1 = __umulhi(m1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t philox_x(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
+                                             uint64_t seed)
+{
+    return philox4x32_10(make_uint4(w0, w1, w2, w3),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)))
+        .x;
+}
+
+// 2^x on the special-function unit (PTX ex2.approx, flush-to-zero).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// First error wins; the host reads it on the next synchronising call.
+__device__ __forceinline__ void set_status(int32_t *status, int32_t code)
+{
+    atomicCAS(status, 0, code);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// One octree node, 32 bytes (one L2 sector): geometry refreshed by every
+// bottom-up update, topology fixed by the build.
+struct __align__(16) NodeGeo {
+    float cx, cy, cz; // count-weighted centroid (0 when count == 0)
+    float cnt;        // vacant dendritic elements, as float
+};
+struct __align__(16) NodeTopo {
+    int32_t escape; // pre-order index just past this node's subtree
+    int32_t meta;   // bits 0..3 depth (0..11), bit 4 leaf
+    int32_t neuron; // leaves: Morton position of the neuron; inner: first position
+    int32_t icount; // vacant dendritic elements, exact
+};
+struct __align__(32) Node {
+    NodeGeo g;
+    NodeTopo t;
+};
+
+constexpr int kLeafBit = 16;
+constexpr int kMaxDepth = 10;
+
+} // namespace rl

@@ -1,0 +1,157 @@
+// Host-side internals of librelearn: the context and the kernel launchers that
+// the translation units share. Not installed; the public ABI is relearn.h.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/relearn.h"
+#include "device.cuh"
+
+namespace rl {
+
+// Scratch of the device-wide exclusive scan (two-level, int64 block sums).
+struct ScanScratch {
+    int64_t *block_sums = nullptr; // [max_blocks + 1]
+    int64_t max_blocks = 0;
+};
+
+// Scratch of the LSD radix sort (per-block digit histograms, digit-major).
+struct SortScratch {
+    int32_t *hist = nullptr;      // [256 * max_blocks]
+    int64_t max_blocks = 0;
+    ScanScratch scan;
+};
+
+// Per-build geometry, device resident.
+struct Geom {
+    float lo[3], hi[3], inv[3];
+    float pad;
+    double ext; // longest edge of the domain box
+};
+
+// Per-update search constants computed on the device from Geom and params.
+struct SearchConst {
+    float thr[12]; // node accepted iff d^2 > thr[depth] (= (len_depth / theta)^2)
+    float k2;      // log2(e) / sigma^2
+    float pad[3];
+};
+
+} // namespace rl
+
+struct relearn_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int64_t max_neurons = 0, max_synapses = 0, max_searches = 0, max_nodes = 0;
+    cudaStream_t last_stream = nullptr;
+    bool built = false;
+    int64_t n = 0; // neurons in the current tree
+    relearn_status host_error = RELEARN_OK;
+    char msg[256] = {0};
+
+    // ---- device scalars (one block, see api.cu for the slot map)
+    int32_t *d_status = nullptr;   // first device error code
+    int64_t *d_i64 = nullptr;      // [16] counters and totals
+    int32_t *d_i32 = nullptr;      // [16] element counts used as kernel bounds
+    rl::Geom *d_geom = nullptr;
+    rl::SearchConst *d_sc = nullptr;
+
+    // ---- tree (per build)
+    uint32_t *d_codes = nullptr, *d_codes_alt = nullptr; // [n]
+    int32_t *d_perm = nullptr, *d_perm_alt = nullptr;    // Morton position -> neuron id
+    float4 *d_pos = nullptr;                             // positions in Morton order
+    uint32_t *d_mask = nullptr;                          // [n] depths of nodes starting here
+    int32_t *d_base = nullptr;                           // [n + 1] pre-order index of position
+    rl::Node *d_nodes = nullptr;                         // [max_nodes]
+    int32_t *d_parent = nullptr, *d_nchild = nullptr;    // [max_nodes]
+    int32_t *d_leaf = nullptr;                           // [n] leaf node of each position
+    double *d_acc = nullptr;                             // [4 * max_nodes] FP64 sums (reduce)
+    int32_t *d_arrive = nullptr;                         // [max_nodes]
+
+    // ---- queries and requests (per update)
+    int32_t *d_cnt = nullptr;       // [n + 1] scratch counts
+    int32_t *d_qoff_s = nullptr;    // [n + 1] query offsets, Morton order
+    int32_t *d_qoff_o = nullptr;    // [n + 1] request offsets, id order
+    int32_t *d_qsrc = nullptr;      // [max_searches] Morton position per query
+    int32_t *d_req_src = nullptr;   // [max_searches] canonical order
+    int32_t *d_req_elem = nullptr;  // [max_searches]
+    int32_t *d_req_tgt = nullptr;   // [max_searches]
+    uint8_t *d_req_acc = nullptr;   // [max_searches]
+    uint32_t *d_req_prio = nullptr; // [max_searches]
+    int32_t *d_bucket = nullptr;    // [max_searches] request ids grouped by target
+    int32_t *d_tcnt = nullptr, *d_toff = nullptr, *d_tfill = nullptr; // [n + 1]
+    int32_t *d_newpos = nullptr;    // [max_searches + 1]
+    double *d_diag_lns = nullptr;   // [max_searches] (diag only)
+    int32_t *d_diag_evals = nullptr, *d_diag_restarts = nullptr;
+
+    // ---- synapse store (canonical by (src, tgt)) and its views
+    int32_t *d_syn_src = nullptr, *d_syn_tgt = nullptr; // [max_synapses]
+    int8_t *d_syn_sign = nullptr;
+    uint64_t *d_key = nullptr, *d_key_alt = nullptr;    // [max_synapses] sort keys
+    int32_t *d_val = nullptr, *d_val_alt = nullptr;     // [max_synapses]
+    uint32_t *d_key32 = nullptr, *d_key32_alt = nullptr;
+    int32_t *d_out_ptr = nullptr, *d_in_ptr = nullptr;  // [max_neurons + 1]
+    int32_t *d_in_src = nullptr, *d_in_syn = nullptr;   // [max_synapses]
+    int8_t *d_in_sign = nullptr;
+    uint32_t *d_prio_ax = nullptr, *d_prio_de = nullptr; // [max_synapses]
+    uint8_t *d_sel_ax = nullptr, *d_sel_de = nullptr;    // [max_synapses]
+    int32_t *d_need_ax = nullptr, *d_need_de = nullptr;  // [max_neurons]
+    int32_t *d_keep = nullptr;                           // [max_synapses + 1]
+
+    rl::ScanScratch scan;
+    rl::SortScratch sort;
+
+    cudaEvent_t ev[8] = {};
+    bool diag_valid = false;
+};
+
+// slots of d_i64 / d_i32
+enum { I64_Q = 0, I64_FAILED, I64_DECLINED, I64_FORMED, I64_NSYN, I64_BROKEN, I64_SCAN_TOTAL,
+       I64_NODES };
+enum { I32_N = 0, I32_Q, I32_NSYN, I32_NEW, I32_NODES, I32_WORK };
+
+namespace rl {
+
+// scan.cu -------------------------------------------------------------------
+// out[i] = sum(in[0 .. i)) for i < count; *total = sum(in[0 .. count)) (int64).
+// count = d_count ? min(*d_count, max_n) : max_n. `out` may alias `in`.
+cudaError_t scan_exclusive(const int32_t *in, int32_t *out, int64_t max_n, const int32_t *d_count,
+                           int64_t *d_total, ScanScratch &s, cudaStream_t st);
+int64_t scan_blocks_needed(int64_t max_n);
+cudaError_t fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t st);
+
+// sort.cu -------------------------------------------------------------------
+// Stable LSD radix sort of (key, val) on bits [0, end_bit). Returns the buffer
+// index holding the result (0: keys/vals, 1: the *_alt buffers) through *which.
+cudaError_t radix_sort_u32(uint32_t *keys, uint32_t *keys_alt, int32_t *vals, int32_t *vals_alt,
+                           int64_t max_n, const int32_t *d_count, int end_bit, SortScratch &s,
+                           cudaStream_t st, int *which);
+cudaError_t radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, int32_t *vals, int32_t *vals_alt,
+                           int64_t max_n, const int32_t *d_count, int end_bit, SortScratch &s,
+                           cudaStream_t st, int *which);
+int64_t sort_blocks_needed(int64_t max_n);
+
+// octree.cu -----------------------------------------------------------------
+cudaError_t octree_build(relearn_ctx *c, int64_t n, const float *x, const float *y,
+                         const float *z, const float *box_lo, const float *box_hi,
+                         cudaStream_t st);
+cudaError_t octree_reduce(relearn_ctx *c, const int32_t *vac_de, cudaStream_t st);
+
+// search.cu -----------------------------------------------------------------
+cudaError_t search_prepare(relearn_ctx *c, const relearn_params &p, const int32_t *vac_ax,
+                           cudaStream_t st);
+cudaError_t search_run(relearn_ctx *c, const relearn_params &p, cudaStream_t st);
+
+// synapses.cu ---------------------------------------------------------------
+cudaError_t accept_requests(relearn_ctx *c, const relearn_params &p, const int32_t *vac_de,
+                            cudaStream_t st);
+cudaError_t apply_requests(relearn_ctx *c, int32_t *vac_ax, int32_t *vac_de, const uint8_t *type,
+                           cudaStream_t st);
+cudaError_t rebuild_views(relearn_ctx *c, cudaStream_t st);
+cudaError_t delete_synapses(relearn_ctx *c, const relearn_params &p, const int32_t *retract_ax,
+                            const int32_t *retract_de, int32_t *vac_ax, int32_t *vac_de,
+                            cudaStream_t st);
+cudaError_t deliver_spikes(relearn_ctx *c, const uint8_t *spiked, int32_t *input,
+                           cudaStream_t st);
+cudaError_t canonicalise_store(relearn_ctx *c, cudaStream_t st);
+
+} // namespace rl

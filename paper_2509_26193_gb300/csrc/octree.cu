@@ -1,0 +1,397 @@
+// Octree build and bottom-up update (Sec. III-B "Spatial octree" and
+// "Division of work").
+//
+// Build: bounding box -> 30-bit Morton codes -> stable radix sort of (code, id)
+// -> compressed octree in pre-order. A node is the root, a cell with >= 2
+// non-empty child cells, or a depth-10 cell with >= 2 neurons (a bucket whose
+// children are its neurons); every neuron is one leaf. A chain of single-child
+// cells holds one neuron set and is stored once, at its deepest cell, which
+// gives the same candidate (count, centroid) and the same restart point as the
+// uncompressed octree. Nodes are laid out in pre-order with a skip link
+// (`escape`) per node so that a search walks the tree without a stack.
+//
+// Reduce: one thread per leaf climbs towards the root; the last child to
+// arrive at a node sums all of that node's children (in Morton order, FP64)
+// and continues upward, so every node is summed once and deterministically.
+#include "internal.h"
+
+namespace rl {
+
+namespace {
+
+__device__ __forceinline__ uint32_t ordered(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unordered(uint32_t u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// d_ord[0..2] = min (ordered), d_ord[3..5] = max (ordered); NaN positions are skipped.
+__global__ void bbox_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                            const float *__restrict__ z, int64_t n, uint32_t *d_ord)
+{
+    uint32_t mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0u, 0u, 0u};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float p[3] = {x[i], y[i], z[i]};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (p[a] != p[a]) continue;
+            uint32_t o = ordered(p[a]);
+            mn[a] = min(mn[a], o);
+            mx[a] = max(mx[a], o);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        for (int off = 16; off; off >>= 1) {
+            mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], off));
+            mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], off));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&d_ord[a], mn[a]);
+            atomicMax(&d_ord[3 + a], mx[a]);
+        }
+    }
+}
+
+__global__ void bbox_init_kernel(uint32_t *d_ord)
+{
+    if (threadIdx.x < 6) d_ord[threadIdx.x] = threadIdx.x < 3 ? 0xffffffffu : 0u;
+}
+
+struct Box {
+    float lo[3], hi[3];
+    int given;
+};
+
+// Domain box, FP32 inverse extents (IEEE division, as the quantisation formula
+// states) and the longest edge in FP64.
+__global__ void geom_kernel(const uint32_t *d_ord, Box box, Geom *g)
+{
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        if (box.given) {
+            lo[a] = box.lo[a];
+            hi[a] = box.hi[a];
+        } else if (d_ord[a] == 0xffffffffu) { // all NaN
+            lo[a] = hi[a] = 0.0f;
+        } else {
+            lo[a] = unordered(d_ord[a]);
+            hi[a] = unordered(d_ord[3 + a]);
+        }
+    }
+    double ext = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        g->lo[a] = lo[a];
+        g->hi[a] = hi[a];
+        float e = __fsub_rn(hi[a], lo[a]);
+        g->inv[a] = e > 0.0f ? __fdiv_rn(1.0f, e) : 0.0f;
+        double ed = (double)hi[a] - (double)lo[a];
+        if (ed > ext) ext = ed;
+    }
+    g->ext = ext;
+}
+
+// Spread the low 10 bits of v to every third bit.
+__device__ __forceinline__ uint32_t spread3(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t quantise(float x, float lo, float inv)
+{
+    float t = __fmul_rn(__fmul_rn(__fsub_rn(x, lo), inv), 1024.0f);
+    t = fminf(fmaxf(t, 0.0f), 1023.0f); // NaN -> 0
+    return __float2uint_rz(t);
+}
+
+__global__ void morton_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                              const float *__restrict__ z, int64_t n, const Geom *__restrict__ g,
+                              uint32_t *__restrict__ codes, int32_t *__restrict__ ids)
+{
+    const float lx = g->lo[0], ly = g->lo[1], lz = g->lo[2];
+    const float ix = g->inv[0], iy = g->inv[1], iz = g->inv[2];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t qx = quantise(x[i], lx, ix), qy = quantise(y[i], ly, iy),
+                 qz = quantise(z[i], lz, iz);
+        codes[i] = spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
+        ids[i] = (int32_t)i;
+    }
+}
+
+__global__ void gather_pos_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                                  const float *__restrict__ z, const int32_t *__restrict__ perm,
+                                  int64_t n, float4 *__restrict__ pos)
+{
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        int32_t i = perm[s];
+        pos[s] = make_float4(x[i], y[i], z[i], 0.0f);
+    }
+}
+
+// Number of leading octal digits shared by codes a and b (10 when equal).
+__device__ __forceinline__ int common_digits(uint32_t a, uint32_t b)
+{
+    uint32_t d = a ^ b;
+    return d ? (__clz(d) - 2) / 3 : 10;
+}
+
+// First index in [lo, hi) with codes[idx] >= key (codes sorted ascending).
+__device__ __forceinline__ int64_t lower_bound(const uint32_t *codes, int64_t lo, int64_t hi,
+                                               uint32_t key)
+{
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (codes[mid] < key)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// First index in [lo, hi) with (codes[idx] >> shift) > prefix.
+__device__ __forceinline__ int64_t upper_bound_prefix(const uint32_t *codes, int64_t lo,
+                                                      int64_t hi, uint32_t prefix, int shift)
+{
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((codes[mid] >> shift) <= prefix)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Each adjacent pair (j, j+1) that first separates two child cells of a depth-d
+// cell (d = common digits) marks that cell as a node: bit d of mask[cell start].
+__global__ void topo_pairs_kernel(const uint32_t *__restrict__ codes, int64_t n,
+                                  uint32_t *__restrict__ mask)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n - 1;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t cj = codes[j];
+        int d = common_digits(cj, codes[j + 1]);
+        int64_t L;
+        if (d == kMaxDepth) {
+            if (j > 0 && codes[j - 1] == cj) continue; // not the first pair of the bucket
+            L = j;
+        } else {
+            int s1 = 3 * (kMaxDepth - 1 - d); // child cell (depth d + 1) prefix
+            uint32_t key = (cj >> s1) << s1;
+            int64_t Lc = lower_bound(codes, 0, j, key);
+            if (Lc > 0 && common_digits(codes[Lc - 1], codes[Lc]) >= d) continue;
+            L = Lc;
+        }
+        atomicOr(&mask[L], 1u << d);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&mask[0], 1u); // the root
+}
+
+__global__ void topo_count_kernel(const uint32_t *__restrict__ mask, int64_t n,
+                                  int32_t *__restrict__ cnt)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        cnt[i] = i < n ? __popc(mask[i]) + 1 : 0;
+}
+
+// Parent of a node whose shallower ancestors do not start at position i: the
+// node of depth common_digits(i-1, i) that contains positions i-1 and i.
+__device__ __forceinline__ int32_t parent_across(const uint32_t *codes, const uint32_t *mask,
+                                                 const int32_t *base, int64_t i, int *pdepth)
+{
+    int dp = common_digits(codes[i - 1], codes[i]);
+    int sh = 3 * (kMaxDepth - dp);
+    uint32_t key = dp == 0 ? 0u : ((codes[i] >> sh) << sh);
+    int64_t Lp = lower_bound(codes, 0, i, key);
+    *pdepth = dp;
+    return base[Lp] + __popc(mask[Lp] & ((1u << dp) - 1u));
+}
+
+__global__ void topo_emit_kernel(const uint32_t *__restrict__ codes, int64_t n,
+                                 const uint32_t *__restrict__ mask,
+                                 const int32_t *__restrict__ base, Node *__restrict__ nodes,
+                                 int32_t *__restrict__ parent, int32_t *__restrict__ nchild,
+                                 int32_t *__restrict__ leaf_of)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t m = mask[i];
+        const int32_t b = base[i];
+        const uint32_t ci = codes[i];
+        int rank = 0;
+        for (uint32_t mm = m; mm; mm &= mm - 1) {
+            int d = __ffs(mm) - 1;
+            int32_t v = b + rank;
+            int sh = 3 * (kMaxDepth - d);
+            int64_t R = d == 0 ? n - 1 : upper_bound_prefix(codes, i, n, ci >> sh, sh) - 1;
+            int32_t par = -1;
+            if (rank > 0) {
+                par = v - 1;
+            } else if (i > 0) {
+                int pd;
+                par = parent_across(codes, mask, base, i, &pd);
+            }
+            Node nd;
+            nd.g = NodeGeo{0.f, 0.f, 0.f, 0.f};
+            nd.t = NodeTopo{base[R + 1], d, (int32_t)i, 0};
+            nodes[v] = nd;
+            parent[v] = par;
+            if (par >= 0) atomicAdd(&nchild[par], 1);
+            ++rank;
+        }
+        // the leaf of position i
+        int32_t v = b + rank;
+        int32_t par;
+        int ldepth;
+        if (m) {
+            par = v - 1;
+            ldepth = 32 - __clz(m); // deepest node at i, plus one
+        } else {
+            int pd;
+            par = parent_across(codes, mask, base, i, &pd);
+            ldepth = pd + 1;
+        }
+        Node nd;
+        nd.g = NodeGeo{0.f, 0.f, 0.f, 0.f};
+        nd.t = NodeTopo{v + 1, ldepth | kLeafBit, (int32_t)i, 0};
+        nodes[v] = nd;
+        parent[v] = par;
+        atomicAdd(&nchild[par], 1);
+        leaf_of[i] = v;
+    }
+}
+
+__global__ void reduce_kernel(Node *__restrict__ nodes, const int32_t *__restrict__ parent,
+                              const int32_t *__restrict__ nchild, int32_t *__restrict__ arrive,
+                              double *__restrict__ acc, const int32_t *__restrict__ leaf_of,
+                              const int32_t *__restrict__ perm, const float4 *__restrict__ pos,
+                              const int32_t *__restrict__ vac_de, int64_t n)
+{
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = leaf_of[s];
+        int32_t c = vac_de[perm[s]];
+        if (c < 0) c = 0;
+        const float4 p = pos[s];
+        const double dc = (double)c;
+        acc[4 * (int64_t)v + 0] = dc;
+        acc[4 * (int64_t)v + 1] = dc * (double)p.x;
+        acc[4 * (int64_t)v + 2] = dc * (double)p.y;
+        acc[4 * (int64_t)v + 3] = dc * (double)p.z;
+        nodes[v].g = c > 0 ? NodeGeo{p.x, p.y, p.z, (float)c} : NodeGeo{0.f, 0.f, 0.f, 0.f};
+        nodes[v].t.icount = c;
+        int32_t u = parent[v];
+        for (int level = 0; u >= 0 && level < 64; ++level) { // <= 12 levels in a valid tree
+            __threadfence();
+            int prev = atomicAdd(&arrive[u], 1);
+            if (prev != nchild[u] - 1) break; // another child finishes this node
+            __threadfence();
+            double sc = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+            const int32_t end = nodes[u].t.escape;
+            for (int32_t ch = u + 1; ch < end; ch = max(nodes[ch].t.escape, ch + 1)) {
+                const double *a = acc + 4 * (int64_t)ch;
+                sc += __ldcg(a + 0);
+                sx += __ldcg(a + 1);
+                sy += __ldcg(a + 2);
+                sz += __ldcg(a + 3);
+            }
+            acc[4 * (int64_t)u + 0] = sc;
+            acc[4 * (int64_t)u + 1] = sx;
+            acc[4 * (int64_t)u + 2] = sy;
+            acc[4 * (int64_t)u + 3] = sz;
+            if (sc > 0.0)
+                nodes[u].g = NodeGeo{__double2float_rn(sx / sc), __double2float_rn(sy / sc),
+                                     __double2float_rn(sz / sc), (float)sc};
+            else
+                nodes[u].g = NodeGeo{0.f, 0.f, 0.f, 0.f};
+            nodes[u].t.icount = (int32_t)sc;
+            u = parent[u];
+        }
+    }
+}
+
+inline unsigned grid_for(int64_t n, int threads, int num_sms)
+{
+    int64_t b = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms * 32;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+} // namespace
+
+cudaError_t octree_build(relearn_ctx *c, int64_t n, const float *x, const float *y,
+                         const float *z, const float *box_lo, const float *box_hi,
+                         cudaStream_t st)
+{
+    cudaError_t e;
+    Box box{};
+    box.given = box_lo && box_hi;
+    if (box.given)
+        for (int a = 0; a < 3; ++a) {
+            box.lo[a] = box_lo[a];
+            box.hi[a] = box_hi[a];
+        }
+    uint32_t *ord = reinterpret_cast<uint32_t *>(c->d_cnt); // 6 words of scratch
+    if (!box.given) {
+        bbox_init_kernel<<<1, 32, 0, st>>>(ord);
+        bbox_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(x, y, z, n, ord);
+    }
+    geom_kernel<<<1, 1, 0, st>>>(ord, box, c->d_geom);
+    morton_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(x, y, z, n, c->d_geom,
+                                                                  c->d_codes, c->d_perm);
+    int which = 0;
+    if ((e = radix_sort_u32(c->d_codes, c->d_codes_alt, c->d_perm, c->d_perm_alt, n, nullptr, 30,
+                            c->sort, st, &which)))
+        return e;
+    if (which) { // keep the sorted result in the primary buffers
+        if ((e = cudaMemcpyAsync(c->d_codes, c->d_codes_alt, n * sizeof(uint32_t),
+                                 cudaMemcpyDeviceToDevice, st)))
+            return e;
+        if ((e = cudaMemcpyAsync(c->d_perm, c->d_perm_alt, n * sizeof(int32_t),
+                                 cudaMemcpyDeviceToDevice, st)))
+            return e;
+    }
+    gather_pos_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(x, y, z, c->d_perm, n,
+                                                                      c->d_pos);
+    if ((e = cudaMemsetAsync(c->d_mask, 0, n * sizeof(uint32_t), st))) return e;
+    topo_pairs_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(c->d_codes, n, c->d_mask);
+    topo_count_kernel<<<grid_for(n + 1, 256, c->num_sms), 256, 0, st>>>(c->d_mask, n, c->d_cnt);
+    if ((e = scan_exclusive(c->d_cnt, c->d_base, n + 1, nullptr, c->d_i64 + I64_NODES, c->scan,
+                            st)))
+        return e;
+    if ((e = cudaMemsetAsync(c->d_nchild, 0, c->max_nodes * sizeof(int32_t), st))) return e;
+    topo_emit_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(
+        c->d_codes, n, c->d_mask, c->d_base, c->d_nodes, c->d_parent, c->d_nchild, c->d_leaf);
+    return cudaGetLastError();
+}
+
+cudaError_t octree_reduce(relearn_ctx *c, const int32_t *vac_de, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->d_arrive, 0, c->max_nodes * sizeof(int32_t), st))) return e;
+    reduce_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(
+        c->d_nodes, c->d_parent, c->d_nchild, c->d_arrive, c->d_acc, c->d_leaf, c->d_perm,
+        c->d_pos, vac_de, c->n);
+    return cudaGetLastError();
+}
+
+} // namespace rl

@@ -1,0 +1,487 @@
+// Acceptance, apply, synapse store, deletion and spike delivery
+// (Sec. III-A "Update of synapses" and "Update of electrical activity").
+//
+// Acceptance groups requests by target with a counting pass (histogram, scan,
+// scatter). A target with no more requests than vacant dendritic elements
+// accepts them all; an over-requested target accepts a request iff fewer than
+// vac_de other requests to it have a smaller (priority, source, element) key,
+// which is the same set as sorting by that key and taking the first vac_de.
+//
+// The store is the synapse multiset in canonical order (source, then target),
+// with an out-row pointer array and an in-view (rows by target, each ordered by
+// source) for deletion and spike delivery.
+#include "internal.h"
+
+namespace rl {
+
+namespace {
+
+inline unsigned grid_for(int64_t n, int threads, int num_sms)
+{
+    int64_t b = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms * 32;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+#define GRID_STRIDE(i, n)                                                                         \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n);                     \
+         i += (int64_t)gridDim.x * blockDim.x)
+
+int id_bits(int64_t n)
+{
+    int b = 1;
+    while (b < 31 && ((int64_t)1 << b) < n) ++b;
+    return b;
+}
+
+// ---------------------------------------------------------------- acceptance
+__global__ void accept_count_kernel(const int32_t *d_Q, const int32_t *__restrict__ req_src,
+                                    const int32_t *__restrict__ req_elem,
+                                    const int32_t *__restrict__ req_tgt,
+                                    uint32_t *__restrict__ prio, int32_t *__restrict__ tcnt,
+                                    uint64_t seed, uint32_t step)
+{
+    const int64_t Q = *d_Q;
+    GRID_STRIDE(r, Q)
+    {
+        int32_t t = req_tgt[r];
+        if (t < 0) continue;
+        atomicAdd(&tcnt[t], 1);
+        prio[r] = philox_x((uint32_t)req_src[r], step, ((uint32_t)req_elem[r] << 8) | 0xFFu, 1u,
+                           seed);
+    }
+}
+
+__global__ void accept_scatter_kernel(const int32_t *d_Q, const int32_t *__restrict__ req_tgt,
+                                      const int32_t *__restrict__ toff,
+                                      int32_t *__restrict__ tfill, int32_t *__restrict__ bucket)
+{
+    const int64_t Q = *d_Q;
+    GRID_STRIDE(r, Q)
+    {
+        int32_t t = req_tgt[r];
+        if (t < 0) continue;
+        bucket[toff[t] + atomicAdd(&tfill[t], 1)] = (int32_t)r;
+    }
+}
+
+__device__ __forceinline__ bool key_less(uint32_t pa, int32_t sa, int32_t ea, uint32_t pb,
+                                         int32_t sb, int32_t eb)
+{
+    if (pa != pb) return pa < pb;
+    if (sa != sb) return sa < sb;
+    return ea < eb;
+}
+
+__global__ void accept_decide_kernel(const int32_t *d_Q, const int32_t *__restrict__ req_src,
+                                     const int32_t *__restrict__ req_elem,
+                                     const int32_t *__restrict__ req_tgt,
+                                     const uint32_t *__restrict__ prio,
+                                     const int32_t *__restrict__ tcnt,
+                                     const int32_t *__restrict__ toff,
+                                     const int32_t *__restrict__ bucket,
+                                     const int32_t *__restrict__ vac_de,
+                                     uint8_t *__restrict__ acc, int64_t *declined)
+{
+    const int64_t Q = *d_Q;
+    int64_t dec = 0;
+    GRID_STRIDE(r, Q)
+    {
+        int32_t t = req_tgt[r];
+        uint8_t a = 0;
+        if (t >= 0) {
+            int32_t v = vac_de[t];
+            if (v < 0) v = 0;
+            int32_t rt = tcnt[t];
+            if (rt <= v) {
+                a = 1;
+            } else if (v > 0) {
+                const uint32_t pr = prio[r];
+                const int32_t sr = req_src[r], er = req_elem[r];
+                int32_t below = 0;
+                const int32_t b0 = toff[t];
+                for (int32_t k = 0; k < rt && below < v; ++k) {
+                    int32_t o = bucket[b0 + k];
+                    if (o != r && key_less(prio[o], req_src[o], req_elem[o], pr, sr, er)) ++below;
+                }
+                a = below < v ? 1 : 0;
+            }
+            dec += a ? 0 : 1;
+        }
+        acc[r] = a;
+    }
+    for (int off = 16; off; off >>= 1) dec += __shfl_xor_sync(0xffffffffu, dec, off);
+    if ((threadIdx.x & 31) == 0 && dec)
+        atomicAdd(reinterpret_cast<unsigned long long *>(declined), (unsigned long long)dec);
+}
+
+// ---------------------------------------------------------------- apply
+__global__ void flags_kernel(const int32_t *d_Q, const uint8_t *__restrict__ acc,
+                             int32_t *__restrict__ out)
+{
+    const int64_t Q = *d_Q;
+    GRID_STRIDE(r, Q) out[r] = acc[r];
+}
+
+// New store size check: formed = *d_formed; nothing is applied on overflow.
+__global__ void apply_check_kernel(const int64_t *d_formed, int32_t *d_nsyn, int32_t *d_new,
+                                   int64_t max_synapses, int32_t *status, int64_t *d_formed_out)
+{
+    int64_t f = *d_formed;
+    if ((int64_t)*d_nsyn + f > max_synapses) {
+        set_status(status, RELEARN_ERR_CAPACITY);
+        *d_new = -1;
+        *d_formed_out = 0;
+    } else {
+        *d_new = (int32_t)f;
+        *d_formed_out = f;
+    }
+}
+
+__global__ void apply_kernel(const int32_t *d_Q, const int32_t *d_new, const int32_t *d_nsyn,
+                             const int32_t *__restrict__ req_src,
+                             const int32_t *__restrict__ req_tgt, const uint8_t *__restrict__ acc,
+                             const int32_t *__restrict__ newpos, const uint8_t *__restrict__ type,
+                             int32_t *vac_ax, int32_t *vac_de, int32_t *__restrict__ syn_src,
+                             int32_t *__restrict__ syn_tgt, int8_t *__restrict__ syn_sign)
+{
+    if (*d_new < 0) return;
+    const int64_t Q = *d_Q;
+    const int32_t base = *d_nsyn;
+    GRID_STRIDE(r, Q)
+    {
+        if (!acc[r]) continue;
+        const int32_t s = req_src[r], t = req_tgt[r];
+        atomicSub(&vac_ax[s], 1);
+        atomicSub(&vac_de[t], 1);
+        const int32_t k = base + newpos[r];
+        syn_src[k] = s;
+        syn_tgt[k] = t;
+        syn_sign[k] = type[s] ? (int8_t)-1 : (int8_t)1;
+    }
+}
+
+__global__ void grow_store_kernel(const int32_t *d_new, int32_t *d_nsyn, int64_t *d_nsyn64)
+{
+    if (*d_new > 0) *d_nsyn += *d_new;
+    *d_nsyn64 = *d_nsyn;
+}
+
+// ---------------------------------------------------------------- store
+__global__ void make_keys_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ src,
+                                 const int32_t *__restrict__ tgt,
+                                 const int8_t *__restrict__ sign, int bits,
+                                 uint64_t *__restrict__ key, int32_t *__restrict__ val)
+{
+    const int64_t m = *d_nsyn;
+    GRID_STRIDE(k, m)
+    {
+        key[k] = ((uint64_t)(uint32_t)src[k] << bits) | (uint32_t)tgt[k];
+        val[k] = sign[k];
+    }
+}
+
+__global__ void unpack_keys_kernel(const int32_t *d_nsyn, const uint64_t *__restrict__ key,
+                                   const int32_t *__restrict__ val, int bits,
+                                   int32_t *__restrict__ src, int32_t *__restrict__ tgt,
+                                   int8_t *__restrict__ sign)
+{
+    const int64_t m = *d_nsyn;
+    const uint64_t mask = ((uint64_t)1 << bits) - 1;
+    GRID_STRIDE(k, m)
+    {
+        uint64_t kk = key[k];
+        src[k] = (int32_t)(kk >> bits);
+        tgt[k] = (int32_t)(kk & mask);
+        sign[k] = (int8_t)val[k];
+    }
+}
+
+__global__ void degree_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ src,
+                              const int32_t *__restrict__ tgt, int32_t *__restrict__ out_cnt,
+                              int32_t *__restrict__ in_cnt, uint32_t *__restrict__ key32,
+                              int32_t *__restrict__ idx)
+{
+    const int64_t m = *d_nsyn;
+    GRID_STRIDE(k, m)
+    {
+        atomicAdd(&out_cnt[src[k]], 1);
+        atomicAdd(&in_cnt[tgt[k]], 1);
+        key32[k] = (uint32_t)tgt[k];
+        idx[k] = (int32_t)k;
+    }
+}
+
+__global__ void in_view_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ order,
+                               const int32_t *__restrict__ src, const int8_t *__restrict__ sign,
+                               int32_t *__restrict__ in_syn, int32_t *__restrict__ in_src,
+                               int8_t *__restrict__ in_sign)
+{
+    const int64_t m = *d_nsyn;
+    GRID_STRIDE(k, m)
+    {
+        int32_t s = order[k];
+        in_syn[k] = s;
+        in_src[k] = src[s];
+        in_sign[k] = sign[s];
+    }
+}
+
+// ---------------------------------------------------------------- deletion
+__global__ void delete_needs_kernel(int64_t n, const int32_t *__restrict__ retract_ax,
+                                    const int32_t *__restrict__ retract_de, int32_t *vac_ax,
+                                    int32_t *vac_de, const int32_t *__restrict__ out_ptr,
+                                    const int32_t *__restrict__ in_ptr,
+                                    int32_t *__restrict__ need_ax, int32_t *__restrict__ need_de)
+{
+    GRID_STRIDE(i, n)
+    {
+        int32_t ra = retract_ax[i] > 0 ? retract_ax[i] : 0;
+        int32_t va = vac_ax[i];
+        int32_t ta = ra < va ? ra : (va > 0 ? va : 0);
+        vac_ax[i] = va - ta;
+        ra -= ta;
+        int32_t deg = out_ptr[i + 1] - out_ptr[i];
+        need_ax[i] = ra < deg ? ra : deg;
+        int32_t rd = retract_de[i] > 0 ? retract_de[i] : 0;
+        int32_t vd = vac_de[i];
+        int32_t td = rd < vd ? rd : (vd > 0 ? vd : 0);
+        vac_de[i] = vd - td;
+        rd -= td;
+        int32_t din = in_ptr[i + 1] - in_ptr[i];
+        need_de[i] = rd < din ? rd : din;
+    }
+}
+
+__global__ void delete_prio_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ src,
+                                   const int32_t *__restrict__ in_syn,
+                                   const int32_t *__restrict__ tgt,
+                                   const int32_t *__restrict__ out_ptr,
+                                   const int32_t *__restrict__ in_ptr,
+                                   uint32_t *__restrict__ prio_ax, uint32_t *__restrict__ prio_de,
+                                   uint8_t *__restrict__ sel_ax, uint8_t *__restrict__ sel_de,
+                                   uint64_t seed, uint32_t step)
+{
+    const int64_t m = *d_nsyn;
+    GRID_STRIDE(k, m)
+    {
+        int32_t i = src[k];
+        prio_ax[k] = philox_x((uint32_t)i, step, (uint32_t)(k - out_ptr[i]), 2u, seed);
+        int32_t j = tgt[in_syn[k]];
+        prio_de[k] = philox_x((uint32_t)j, step, (uint32_t)(k - in_ptr[j]), 3u, seed);
+        sel_ax[k] = 0;
+        sel_de[k] = 0;
+    }
+}
+
+// Row i picks its `need` slots with the smallest (priority, slot).
+__global__ void delete_select_kernel(int64_t n, const int32_t *__restrict__ ptr,
+                                     const int32_t *__restrict__ need,
+                                     const uint32_t *__restrict__ prio,
+                                     const int32_t *__restrict__ map, uint8_t *__restrict__ sel)
+{
+    GRID_STRIDE(i, n)
+    {
+        const int32_t want = need[i];
+        if (want <= 0) continue;
+        const int32_t b = ptr[i], deg = ptr[i + 1] - b;
+        for (int32_t k = 0; k < deg; ++k) {
+            const uint32_t pk = prio[b + k];
+            int32_t below = 0;
+            for (int32_t o = 0; o < deg && below < want; ++o) {
+                uint32_t po = prio[b + o];
+                if (po < pk || (po == pk && o < k)) ++below;
+            }
+            if (below < want) sel[map ? map[b + k] : b + k] = 1;
+        }
+    }
+}
+
+__global__ void delete_apply_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ src,
+                                    const int32_t *__restrict__ tgt,
+                                    const uint8_t *__restrict__ sel_ax,
+                                    const uint8_t *__restrict__ sel_de, int32_t *vac_ax,
+                                    int32_t *vac_de, int32_t *__restrict__ keep)
+{
+    const int64_t m = *d_nsyn;
+    GRID_STRIDE(k, m)
+    {
+        const bool a = sel_ax[k], d = sel_de[k];
+        if (a && !d) atomicAdd(&vac_de[tgt[k]], 1);
+        if (d && !a) atomicAdd(&vac_ax[src[k]], 1);
+        keep[k] = (a || d) ? 0 : 1;
+    }
+}
+
+__global__ void compact_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ src,
+                               const int32_t *__restrict__ tgt, const int8_t *__restrict__ sign,
+                               const uint8_t *__restrict__ sel_ax,
+                               const uint8_t *__restrict__ sel_de,
+                               const int32_t *__restrict__ pos, int bits,
+                               uint64_t *__restrict__ key, int32_t *__restrict__ val)
+{
+    const int64_t m = *d_nsyn;
+    GRID_STRIDE(k, m)
+    {
+        if (sel_ax[k] || sel_de[k]) continue;
+        int32_t w = pos[k];
+        key[w] = ((uint64_t)(uint32_t)src[k] << bits) | (uint32_t)tgt[k];
+        val[w] = sign[k];
+    }
+}
+
+__global__ void shrink_store_kernel(int32_t *d_nsyn, const int64_t *d_kept, int64_t *d_broken,
+                                    int64_t *d_nsyn64)
+{
+    int64_t kept = *d_kept;
+    *d_broken = (int64_t)*d_nsyn - kept;
+    *d_nsyn = (int32_t)kept;
+    *d_nsyn64 = kept;
+}
+
+// ---------------------------------------------------------------- spikes
+__global__ void spikes_kernel(int64_t n, const int32_t *__restrict__ in_ptr,
+                              const int32_t *__restrict__ in_src,
+                              const int8_t *__restrict__ in_sign,
+                              const uint8_t *__restrict__ spiked, int32_t *__restrict__ input)
+{
+    GRID_STRIDE(t, n)
+    {
+        int32_t acc = 0;
+        const int32_t b = in_ptr[t], e = in_ptr[t + 1];
+        for (int32_t k = b; k < e; ++k) acc += spiked[in_src[k]] ? (int32_t)in_sign[k] : 0;
+        input[t] = acc;
+    }
+}
+
+} // namespace
+
+cudaError_t accept_requests(relearn_ctx *c, const relearn_params &p, const int32_t *vac_de,
+                            cudaStream_t st)
+{
+    cudaError_t e;
+    const int64_t n = c->n;
+    const int32_t *dQ = c->d_i32 + I32_Q;
+    const unsigned gq = grid_for(c->max_searches, 256, c->num_sms);
+    if ((e = cudaMemsetAsync(c->d_tcnt, 0, (n + 1) * sizeof(int32_t), st))) return e;
+    if ((e = cudaMemsetAsync(c->d_tfill, 0, (n + 1) * sizeof(int32_t), st))) return e;
+    if ((e = cudaMemsetAsync(c->d_i64 + I64_DECLINED, 0, sizeof(int64_t), st))) return e;
+    accept_count_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_src, c->d_req_elem, c->d_req_tgt,
+                                            c->d_req_prio, c->d_tcnt, p.seed, (uint32_t)p.step);
+    if ((e = scan_exclusive(c->d_tcnt, c->d_toff, n + 1, nullptr, nullptr, c->scan, st))) return e;
+    accept_scatter_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_tgt, c->d_toff, c->d_tfill,
+                                              c->d_bucket);
+    accept_decide_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_src, c->d_req_elem, c->d_req_tgt,
+                                             c->d_req_prio, c->d_tcnt, c->d_toff, c->d_bucket,
+                                             vac_de, c->d_req_acc, c->d_i64 + I64_DECLINED);
+    return cudaGetLastError();
+}
+
+cudaError_t canonicalise_store(relearn_ctx *c, cudaStream_t st)
+{
+    cudaError_t e;
+    const int bits = id_bits(c->max_neurons);
+    const int32_t *dm = c->d_i32 + I32_NSYN;
+    const unsigned gs = grid_for(c->max_synapses, 256, c->num_sms);
+    make_keys_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_syn_tgt, c->d_syn_sign, bits,
+                                         c->d_key, c->d_val);
+    int which = 0;
+    if ((e = radix_sort_u64(c->d_key, c->d_key_alt, c->d_val, c->d_val_alt, c->max_synapses, dm,
+                            2 * bits, c->sort, st, &which)))
+        return e;
+    unpack_keys_kernel<<<gs, 256, 0, st>>>(dm, which ? c->d_key_alt : c->d_key,
+                                           which ? c->d_val_alt : c->d_val, bits, c->d_syn_src,
+                                           c->d_syn_tgt, c->d_syn_sign);
+    return rebuild_views(c, st);
+}
+
+cudaError_t rebuild_views(relearn_ctx *c, cudaStream_t st)
+{
+    cudaError_t e;
+    const int64_t n = c->n;
+    const int bits = id_bits(c->max_neurons);
+    const int32_t *dm = c->d_i32 + I32_NSYN;
+    const unsigned gs = grid_for(c->max_synapses, 256, c->num_sms);
+    int32_t *out_cnt = c->d_cnt, *in_cnt = c->d_tcnt;
+    if ((e = cudaMemsetAsync(out_cnt, 0, (n + 1) * sizeof(int32_t), st))) return e;
+    if ((e = cudaMemsetAsync(in_cnt, 0, (n + 1) * sizeof(int32_t), st))) return e;
+    degree_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_syn_tgt, out_cnt, in_cnt, c->d_key32,
+                                      c->d_val);
+    if ((e = scan_exclusive(out_cnt, c->d_out_ptr, n + 1, nullptr, nullptr, c->scan, st)))
+        return e;
+    if ((e = scan_exclusive(in_cnt, c->d_in_ptr, n + 1, nullptr, nullptr, c->scan, st))) return e;
+    int which = 0;
+    if ((e = radix_sort_u32(c->d_key32, c->d_key32_alt, c->d_val, c->d_val_alt, c->max_synapses,
+                            dm, bits, c->sort, st, &which)))
+        return e;
+    in_view_kernel<<<gs, 256, 0, st>>>(dm, which ? c->d_val_alt : c->d_val, c->d_syn_src,
+                                       c->d_syn_sign, c->d_in_syn, c->d_in_src, c->d_in_sign);
+    return cudaGetLastError();
+}
+
+cudaError_t apply_requests(relearn_ctx *c, int32_t *vac_ax, int32_t *vac_de, const uint8_t *type,
+                           cudaStream_t st)
+{
+    cudaError_t e;
+    const int32_t *dQ = c->d_i32 + I32_Q;
+    const unsigned gq = grid_for(c->max_searches, 256, c->num_sms);
+    flags_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_acc, c->d_newpos);
+    if ((e = scan_exclusive(c->d_newpos, c->d_newpos, c->max_searches, dQ,
+                            c->d_i64 + I64_SCAN_TOTAL, c->scan, st)))
+        return e;
+    apply_check_kernel<<<1, 1, 0, st>>>(c->d_i64 + I64_SCAN_TOTAL, c->d_i32 + I32_NSYN,
+                                        c->d_i32 + I32_NEW, c->max_synapses, c->d_status,
+                                        c->d_i64 + I64_FORMED);
+    apply_kernel<<<gq, 256, 0, st>>>(dQ, c->d_i32 + I32_NEW, c->d_i32 + I32_NSYN, c->d_req_src,
+                                     c->d_req_tgt, c->d_req_acc, c->d_newpos, type, vac_ax,
+                                     vac_de, c->d_syn_src, c->d_syn_tgt, c->d_syn_sign);
+    grow_store_kernel<<<1, 1, 0, st>>>(c->d_i32 + I32_NEW, c->d_i32 + I32_NSYN,
+                                       c->d_i64 + I64_NSYN);
+    return canonicalise_store(c, st);
+}
+
+cudaError_t delete_synapses(relearn_ctx *c, const relearn_params &p, const int32_t *retract_ax,
+                            const int32_t *retract_de, int32_t *vac_ax, int32_t *vac_de,
+                            cudaStream_t st)
+{
+    cudaError_t e;
+    const int64_t n = c->n;
+    const int bits = id_bits(c->max_neurons);
+    const int32_t *dm = c->d_i32 + I32_NSYN;
+    const unsigned gs = grid_for(c->max_synapses, 256, c->num_sms);
+    const unsigned gn = grid_for(n, 256, c->num_sms);
+    delete_needs_kernel<<<gn, 256, 0, st>>>(n, retract_ax, retract_de, vac_ax, vac_de,
+                                            c->d_out_ptr, c->d_in_ptr, c->d_need_ax,
+                                            c->d_need_de);
+    delete_prio_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_in_syn, c->d_syn_tgt,
+                                           c->d_out_ptr, c->d_in_ptr, c->d_prio_ax, c->d_prio_de,
+                                           c->d_sel_ax, c->d_sel_de, p.seed, (uint32_t)p.step);
+    delete_select_kernel<<<gn, 256, 0, st>>>(n, c->d_out_ptr, c->d_need_ax, c->d_prio_ax, nullptr,
+                                             c->d_sel_ax);
+    delete_select_kernel<<<gn, 256, 0, st>>>(n, c->d_in_ptr, c->d_need_de, c->d_prio_de,
+                                             c->d_in_syn, c->d_sel_de);
+    delete_apply_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_syn_tgt, c->d_sel_ax,
+                                            c->d_sel_de, vac_ax, vac_de, c->d_keep);
+    if ((e = scan_exclusive(c->d_keep, c->d_keep, c->max_synapses, dm, c->d_i64 + I64_SCAN_TOTAL,
+                            c->scan, st)))
+        return e;
+    compact_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_syn_tgt, c->d_syn_sign, c->d_sel_ax,
+                                       c->d_sel_de, c->d_keep, bits, c->d_key, c->d_val);
+    shrink_store_kernel<<<1, 1, 0, st>>>(c->d_i32 + I32_NSYN, c->d_i64 + I64_SCAN_TOTAL,
+                                         c->d_i64 + I64_BROKEN, c->d_i64 + I64_NSYN);
+    unpack_keys_kernel<<<gs, 256, 0, st>>>(dm, c->d_key, c->d_val, bits, c->d_syn_src,
+                                           c->d_syn_tgt, c->d_syn_sign);
+    return rebuild_views(c, st);
+}
+
+cudaError_t deliver_spikes(relearn_ctx *c, const uint8_t *spiked, int32_t *input,
+                           cudaStream_t st)
+{
+    spikes_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(
+        c->n, c->d_in_ptr, c->d_in_src, c->d_in_sign, spiked, input);
+    return cudaGetLastError();
+}
+
+} // namespace rl

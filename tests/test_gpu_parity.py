@@ -1,0 +1,281 @@
+"""GPU (CUDA path through the C ABI) against the FP64 oracle.
+
+Integers bit-exact (Morton order, topology, counts, requests outside the
+exemption, accept flags, synapse lists, vacancies, spike inputs); floats within
+the stated tolerances (centroids 1e-6 relative = FP32 rounding of the FP64 sum,
+root-frontier ln S within 1e-5 = 1e-5 relative attraction sum).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import LNS_TOL, GpuNet, compare_targets, dev
+from paper_2509_26193_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2509_26193_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def test_philox_matches_oracle():
+    import torch
+    from paper_2509_26193_gb300 import relearn as R
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, (1000, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, (1000, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[0], key[0] = 0, 0
+    out = torch.zeros(4000, dtype=torch.int32, device="cuda")
+    R.relearn_philox4x32_10(dev(ctr.view(np.int32).ravel()), dev(key.view(np.int32).ravel()), out)
+    got = out.cpu().numpy().view(np.uint32).reshape(1000, 4)
+    assert [hex(v) for v in got[0]] == ["0x6627e8d5", "0xe169c58d", "0xbc57ac4c", "0x9b00dbd8"]
+    for k in range(0, 1000, 37):
+        assert np.array_equal(got[k], oracle.philox4x32_10(ctr[k], key[k]))
+
+
+def _tree_case(name):
+    if name == "cube4096":
+        return workloads.uniform_cube(n=4096, seed=1), None
+    if name == "clusters_ragged":
+        return workloads.gaussian_clusters(n=60001, clusters=7, side=3000, std=120, seed=41), None
+    if name == "slab":
+        return workloads.cortical_slab(n=20000, sx=2000, sy=2000, sz=250, seed=42), None
+    if name == "coincident":
+        net = workloads.uniform_cube(n=3000, seed=43)
+        k = np.arange(0, 3000, 3)
+        net.x[k], net.y[k], net.z[k] = net.x[0], net.y[0], net.z[0]   # one big bucket
+        net.x[1:40:2] = net.x[1]
+        net.y[1:40:2] = net.y[1]
+        net.z[1:40:2] = net.z[1]
+        return net, None
+    if name == "box_clamp":
+        net = workloads.uniform_cube(n=5000, side=1000, seed=44)
+        return net, (np.array([100, 100, 100], np.float32), np.array([900, 800, 950], np.float32))
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["cube4096", "clusters_ragged", "slab", "coincident",
+                                  "box_clamp"])
+def test_tree_matches_oracle(name):
+    net, box = _tree_case(name)
+    g = GpuNet(net, box=box)
+    from paper_2509_26193_gb300 import relearn as R
+    gt = R.relearn_get_tree(g.ctx)
+    t = oracle.Tree(net.x, net.y, net.z, *(box if box else (None, None)))
+    t.reduce(net.vac_de)
+    ot = t.export(compressed=True)
+    assert np.array_equal(gt["perm"], t.canonical_order())
+    for k in ("depth", "first", "size", "is_leaf", "neuron"):
+        assert np.array_equal(gt[k], ot[k]), k
+    assert np.array_equal(gt["count"], ot["count"].astype(np.int32))
+    has = ot["count"] > 0
+    for a in ("cx", "cy", "cz"):
+        ref = ot[a][has]
+        assert np.allclose(gt[a][has], ref, rtol=1e-6, atol=1e-6 * np.abs(ref).max())
+    g.close()
+
+
+def _oracle_searches(net, tree, step, theta, qi=None, qe=None):
+    if qi is None:
+        qi, qe = oracle.queries(net.vac_ax)
+    return qi, qe, tree.search_batch(net.sigma, theta, net.seed, step, qi, qe, threads=8)
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.0, 0.5, 0.2])
+def test_search_matches_oracle_4096(theta):
+    net = workloads.uniform_cube(n=4096, seed=1)
+    g = GpuNet(net)
+    t = oracle.Tree(net.x, net.y, net.z)
+    t.reduce(net.vac_de)
+    stats = g.update(step=3, theta=theta)
+    gt, gacc = g.requests()
+    qi, qe, (ot, od) = _oracle_searches(net, t, 3, theta)
+    assert stats["searches"] == len(qi) == len(gt)
+    bad, exempt, exempt_diff = compare_targets(gt, ot, od)
+    assert bad == 0, (bad, exempt, exempt_diff)
+    assert exempt_diff <= max(2, exempt // 10)
+    from paper_2509_26193_gb300 import relearn as R
+    dg = R.relearn_get_search_diag(g.ctx)
+    fin = np.isfinite(od["ln_s0"])
+    assert np.array_equal(np.isfinite(dg["ln_s0"]), fin)
+    assert np.abs(dg["ln_s0"][fin] - od["ln_s0"][fin]).max() < LNS_TOL
+    same = gt == ot
+    # node evaluations (algorithmic work) agree where the paths agree
+    assert np.mean(dg["evals"][same] == od["evals"][same]) > 0.99
+    assert stats["failed"] == int((gt < 0).sum())
+    g.close()
+
+
+def test_accept_apply_match_oracle_replay():
+    net = workloads.gaussian_clusters(n=30000, clusters=5, side=2500, std=150, seed=51,
+                                      sigma=300.0)
+    g = GpuNet(net)
+    stats = g.update(step=0)
+    gt, gacc = g.requests()
+    qi, qe = oracle.queries(net.vac_ax)
+    # acceptance replayed on the GPU's requests: bit-exact
+    oacc = oracle.accept(net.n, qi, qe, gt, net.vac_de, net.seed, 0)
+    assert np.array_equal(gacc, oacc)
+    assert stats["requests_declined"] == int(((gt >= 0) & (gacc == 0)).sum())
+    # apply: vacancies and the synapse store
+    va, vd = net.vac_ax.copy(), net.vac_de.copy()
+    syn = oracle.Synapses(4 * len(qi) + 16)
+    formed = oracle.apply(qi, gt, oacc, net.type, va, vd, syn)
+    assert stats["formed"] == formed
+    ga, gd = g.vacancies()
+    assert np.array_equal(ga, va) and np.array_equal(gd, vd)
+    s, d, sg = g.synapses()
+    os_, od_, osg = syn.arrays()
+    assert np.array_equal(s, os_) and np.array_equal(d, od_) and np.array_equal(sg, osg)
+    g.close()
+
+
+def test_multistep_update_delete_spikes():
+    """Three updates, each followed by spike delivery, then deletion; the oracle
+    is re-synchronised to the GPU's requests at each step (replay)."""
+    import torch
+    from paper_2509_26193_gb300 import relearn as R
+    net = workloads.gaussian_clusters(n=50000, clusters=9, side=4000, std=200, seed=61,
+                                      sigma=400.0)
+    g = GpuNet(net, max_synapses=400000)
+    t = oracle.Tree(net.x, net.y, net.z)
+    va, vd = net.vac_ax.copy(), net.vac_de.copy()
+    syn = oracle.Synapses(400000)
+    for step in range(3):
+        t.reduce(vd)
+        qi, qe = oracle.queries(va)
+        g.update(step=step)
+        gt, gacc = g.requests()
+        ot, od = t.search_batch(net.sigma, net.theta, net.seed, step, qi, qe, threads=8)
+        bad, exempt, exempt_diff = compare_targets(gt, ot, od)
+        assert bad == 0
+        oacc = oracle.accept(net.n, qi, qe, gt, vd, net.seed, step)
+        assert np.array_equal(gacc, oacc)
+        oracle.apply(qi, gt, oacc, net.type, va, vd, syn)
+        ga, gd = g.vacancies()
+        assert np.array_equal(ga, va) and np.array_equal(gd, vd)
+        s, d, sg = g.synapses()
+        assert np.array_equal(np.stack([s, d, sg]), np.stack(syn.arrays()))
+        spk = workloads.spikes(net.n, net.seed, step)
+        out = torch.zeros(net.n, dtype=torch.int32, device="cuda")
+        R.relearn_deliver_spikes(g.ctx, dev(spk), out)
+        assert np.array_equal(out.cpu().numpy(), oracle.deliver_spikes(net.n, syn, spk))
+    ra, rd = workloads.retractions(net.n, net.seed, 7, lam=1.0)
+    p = R.params(net.sigma, net.theta, net.seed, 7)
+    broken = R.relearn_delete_synapses(g.ctx, p, dev(ra), dev(rd), g.vac_ax, g.vac_de, count=True)
+    obroken = oracle.delete(ra, rd, va, vd, net.seed, 7, syn)
+    assert broken == obroken > 0
+    ga, gd = g.vacancies()
+    assert np.array_equal(ga, va) and np.array_equal(gd, vd)
+    s, d, sg = g.synapses()
+    assert np.array_equal(np.stack([s, d, sg]), np.stack(syn.arrays()))
+    spk = workloads.spikes(net.n, net.seed, 9)
+    out = torch.zeros(net.n, dtype=torch.int32, device="cuda")
+    R.relearn_deliver_spikes(g.ctx, dev(spk), out)
+    assert np.array_equal(out.cpu().numpy(), oracle.deliver_spikes(net.n, syn, spk))
+    g.close()
+
+
+def test_full_size_sampled_2p20():
+    """The benchmark workload (2^20 neurons, 64 clusters), sampled searches."""
+    net = workloads.gaussian_clusters()
+    g = GpuNet(net)
+    stats = g.update(step=0)
+    gt, gacc = g.requests()
+    qi, qe = oracle.queries(net.vac_ax)
+    assert stats["searches"] == len(qi)
+    t = oracle.Tree(net.x, net.y, net.z)
+    t.reduce(net.vac_de)
+    rng = np.random.default_rng(5)
+    sel = np.sort(rng.choice(len(qi), 3000, replace=False))
+    ot, od = t.search_batch(net.sigma, net.theta, net.seed, 0, qi[sel], qe[sel], threads=8)
+    bad, exempt, exempt_diff = compare_targets(gt[sel], ot, od)
+    assert bad == 0, (bad, exempt, exempt_diff)
+    from paper_2509_26193_gb300 import relearn as R
+    dg = R.relearn_get_search_diag(g.ctx)
+    assert np.abs(dg["ln_s0"][sel] - od["ln_s0"]).max() < LNS_TOL
+    # acceptance on every request: bit-exact
+    oacc = oracle.accept(net.n, qi, qe, gt, net.vac_de, net.seed, 0)
+    assert np.array_equal(gacc, oacc)
+    g.close()
+
+
+def test_edge_cases():
+    from paper_2509_26193_gb300 import relearn as R
+    # one neuron: every search fails
+    net = workloads.uniform_cube(n=1, seed=70)
+    net.vac_ax[:] = 3
+    net.vac_de[:] = 2
+    g = GpuNet(net)
+    st = g.update(step=0)
+    assert st["searches"] == 3 and st["failed"] == 3 and st["formed"] == 0
+    g.close()
+    # two neurons: each picks the other
+    net = workloads.uniform_cube(n=2, seed=71)
+    net.vac_ax[:] = [2, 1]
+    net.vac_de[:] = [5, 5]
+    g = GpuNet(net)
+    g.update(step=0)
+    gt, acc = g.requests()
+    assert list(gt) == [1, 1, 0] and acc.all()
+    g.close()
+    # nothing to search
+    net = workloads.uniform_cube(n=1000, seed=72)
+    net.vac_ax[:] = 0
+    g = GpuNet(net)
+    st = g.update(step=0)
+    assert st["searches"] == 0 and st["formed"] == 0
+    g.close()
+    # no vacant dendrites anywhere: every search fails
+    net = workloads.uniform_cube(n=1000, seed=73)
+    net.vac_de[:] = 0
+    g = GpuNet(net)
+    st = g.update(step=0)
+    assert st["failed"] == st["searches"] > 0 and st["formed"] == 0
+    g.close()
+
+
+def test_capacity_overflow_is_reported_and_nothing_applied():
+    from paper_2509_26193_gb300 import relearn as R
+    net = workloads.uniform_cube(n=2000, seed=80)
+    g = GpuNet(net, max_searches=100)
+    with pytest.raises(R.RelearnError) as ei:
+        g.update(step=0)
+    assert ei.value.status == R.ERR_CAPACITY
+    ga, gd = g.vacancies()
+    assert np.array_equal(ga, net.vac_ax) and np.array_equal(gd, net.vac_de)
+    g.close()
+    g = GpuNet(net, max_synapses=10)
+    with pytest.raises(R.RelearnError) as ei:
+        g.update(step=0)
+    assert ei.value.status == R.ERR_CAPACITY
+    ga, gd = g.vacancies()
+    assert np.array_equal(ga, net.vac_ax) and np.array_equal(gd, net.vac_de)
+    assert len(g.synapses()[0]) == 0
+    g.close()
+
+
+def test_checkpoint_resume_is_bit_identical():
+    from paper_2509_26193_gb300 import relearn as R
+    net = workloads.gaussian_clusters(n=20000, clusters=4, side=2000, std=150, seed=90,
+                                      sigma=300.0)
+    a = GpuNet(net)
+    a.update(step=0)
+    s, d, sg = a.synapses()
+    va, vd = a.vacancies()
+    a.update(step=1)
+    want = a.synapses(), a.vacancies()
+    b = GpuNet(net)
+    R.relearn_set_synapses(b.ctx, s[::-1].copy(), d[::-1].copy(), sg[::-1].copy())
+    b.vac_ax.copy_(dev(va))
+    b.vac_de.copy_(dev(vd))
+    b.update(step=1)
+    got = b.synapses(), b.vacancies()
+    for x, y in zip(want[0] + want[1], got[0] + got[1]):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
