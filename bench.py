@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark of the MSP Barnes-Hut connectivity update on GB300.
+
+Metric: neuron-searches per second per connectivity update on the 2^20-neuron
+workload (64 isotropic Gaussian clusters, std 300 um, centres uniform in a 10 mm
+cube, Poisson(2) vacancies clipped to 0..8, sigma = 750 um, theta = 0.3).
+
+One step = one pass of the whole path over that network, starting from empty
+connectivity: octree build (Morton codes, sort, topology), 10 consecutive
+connectivity updates (bottom-up update, Barnes-Hut search, acceptance, apply),
+each followed by spike delivery (5 % of neurons spiking), then a deletion pass
+in which every element is retracted, which returns the network to empty so
+that every step does the same work. value = searches of all 10 updates / step
+time (device time, CUDA events); L2 is flushed between steps.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "neuron-searches/sec per connectivity update at 2^20 neurons; % of GB300 roofline"
+UNIT = "neuron-searches/s"
+UPDATES_PER_STEP = 10
+FLOPS_PER_EVAL = 12            # d^2 (3 sub + 3 fma/mul), criterion, shifted exponent, count, sum
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--theta", type=float, default=0.3)
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_2509_26193_gb300 import workloads
+    return workloads.gaussian_clusters(n=n)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def workload_config(net, theta, extra=None):
+    cfg = {"workload": f"gaussian_clusters n={net.n} (64 clusters, std 300 um, 10 mm cube, "
+                       f"Poisson(2) vacancies 0..8, 20% inhibitory)",
+           "n": net.n, "sigma_um": net.sigma, "theta": theta,
+           "updates_per_step": UPDATES_PER_STEP,
+           "step": "build + 10 x (update + spike delivery) + full deletion",
+           "l2": "flushed between steps (256 MB write)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------- distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(local_units, local_seconds, world, backend_device=None):
+    """Whole-job value: units of all ranks / the slowest rank's time (replicas)."""
+    import torch
+    import torch.distributed as dist
+    if world <= 1:
+        return local_units, local_seconds
+    dev = backend_device or "cpu"
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=dev)
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- our arm
+class Runner:
+    def __init__(self, net, theta, device):
+        import torch
+        from paper_2509_26193_gb300 import build, relearn as R, workloads
+        build.build()
+        self.torch, self.R, self.net, self.theta = torch, R, net, theta
+        self.dev = device
+        n = net.n
+        d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        self.x, self.y, self.z = d(net.x), d(net.y), d(net.z)
+        self.vac_ax0, self.vac_de0 = d(net.vac_ax), d(net.vac_de)
+        self.vac_ax, self.vac_de = self.vac_ax0.clone(), self.vac_de0.clone()
+        self.type = d(net.type)
+        self.spk_host = [workloads.spikes(n, net.seed, u) for u in range(UPDATES_PER_STEP)]
+        self.spiked = [d(s) for s in self.spk_host]
+        self.retract_host = np.full(n, 1 << 20, np.int32)
+        self.retract = d(self.retract_host)
+        self.input = torch.zeros(n, dtype=torch.int32, device=device)
+        cap = int(min(net.vac_ax.sum(), net.vac_de.sum())) + 1024
+        self.ctx = R.relearn_create(n, cap, 0, device=device.index)
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+        # pinned host copies for the end-to-end variant
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        self.h = {"x": pin(net.x), "y": pin(net.y), "z": pin(net.z), "vac_ax": pin(net.vac_ax),
+                  "vac_de": pin(net.vac_de), "type": pin(net.type),
+                  "spiked": [pin(s) for s in self.spk_host], "retract": pin(self.retract_host)}
+        self.h_out = torch.empty(n, dtype=torch.int32).pin_memory()
+        self.h_cnt = torch.empty(2, dtype=torch.int64).pin_memory()
+        self.step_index = 0
+
+    def h2d_bytes(self):
+        n = self.net.n
+        return 12 * n + 8 * n + n + UPDATES_PER_STEP * n + 4 * n
+
+    def d2h_bytes(self):
+        return 4 * self.net.n + 16
+
+    def step(self, e2e=False):
+        R, torch = self.R, self.torch
+        if e2e:  # this step's inputs arrive from pinned host memory
+            for name, dst in (("x", self.x), ("y", self.y), ("z", self.z),
+                              ("vac_ax", self.vac_ax), ("vac_de", self.vac_de),
+                              ("type", self.type), ("retract", self.retract)):
+                dst.copy_(self.h[name], non_blocking=True)
+            for u in range(UPDATES_PER_STEP):
+                self.spiked[u].copy_(self.h["spiked"][u], non_blocking=True)
+        else:    # element-model output for this step: the initial vacancies
+            self.vac_ax.copy_(self.vac_ax0)
+            self.vac_de.copy_(self.vac_de0)
+        R.relearn_build_octree(self.ctx, self.x, self.y, self.z)
+        base = 1000 * self.step_index
+        for u in range(UPDATES_PER_STEP):
+            p = R.params(self.net.sigma, self.theta, self.net.seed, base + u, R.FLAG_TIMING)
+            R.relearn_update_connectivity(self.ctx, p, self.vac_ax, self.vac_de, self.type)
+            R.relearn_deliver_spikes(self.ctx, self.spiked[u], self.input)
+        p = R.params(self.net.sigma, self.theta, self.net.seed, base + 999)
+        R.relearn_delete_synapses(self.ctx, p, self.retract, self.retract, self.vac_ax,
+                                  self.vac_de)
+        if e2e:
+            self.h_out.copy_(self.input, non_blocking=True)
+        self.step_index += 1
+
+    def counters(self):
+        s = self.R.relearn_get_last_stats(self.ctx)
+        return s["searches_total"], s["evals_total"]
+
+    def timed(self, steps, e2e):
+        torch = self.torch
+        st = torch.cuda.current_stream()
+        total_ms = 0.0
+        q0, e0 = self.counters()
+        self.R.relearn_collect_search_times(self.ctx)
+        k_ms, k_n = 0.0, 0
+        l0 = self.R.relearn_launch_count()
+        for _ in range(steps):
+            self.flush.zero_()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            self.step(e2e=e2e)
+            b.record(st)
+            torch.cuda.synchronize()
+            total_ms += a.elapsed_time(b)
+            ms, kn = self.R.relearn_collect_search_times(self.ctx)
+            k_ms += ms
+            k_n += kn
+        launches = self.R.relearn_launch_count() - l0
+        q1, e1 = self.counters()
+        return {"ms": total_ms, "searches": q1 - q0, "evals": e1 - e0, "kernel_ms": k_ms,
+                "kernel_launches": k_n, "launches": launches}
+
+
+def first_update_profile(runner):
+    """Phase times of the first (largest) update of a step, for the breakdown."""
+    R = runner.R
+    runner.vac_ax.copy_(runner.vac_ax0)
+    runner.vac_de.copy_(runner.vac_de0)
+    R.relearn_build_octree(runner.ctx, runner.x, runner.y, runner.z)
+    p = R.params(runner.net.sigma, runner.theta, runner.net.seed, 0)
+    s = R.relearn_update_connectivity(runner.ctx, p, runner.vac_ax, runner.vac_de, runner.type,
+                                      stats=True)
+    p = R.params(runner.net.sigma, runner.theta, runner.net.seed, 999)
+    R.relearn_delete_synapses(runner.ctx, p, runner.retract, runner.retract, runner.vac_ax,
+                              runner.vac_de)
+    runner.torch.cuda.synchronize()
+    return s
+
+
+# ------------------------------------------------------------------ CPU side
+def cpu_baseline(net, theta, sample=1 << 17):
+    """The FP64 oracle on the host cores: tree build + bottom-up update + a random
+    sample of the first update's searches, extrapolated to the whole update."""
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    if not oracle.openmp_available():
+        threads = 1
+    t0 = time.perf_counter()
+    t = oracle.Tree(net.x, net.y, net.z)
+    t1 = time.perf_counter()
+    t.reduce(net.vac_de)
+    t2 = time.perf_counter()
+    qi, qe = oracle.queries(net.vac_ax)
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(len(qi), min(sample, len(qi)), replace=False))
+    t3 = time.perf_counter()
+    _, diag = t.search_batch(net.sigma, theta, net.seed, 0, qi[sel], qe[sel], threads=threads)
+    t4 = time.perf_counter()
+    q = len(qi)
+    est = (t1 - t0) + (t2 - t1) + (t4 - t3) * q / len(sel)
+    return {"value": q / est, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"2^20 octree build + bottom-up update + {len(sel)} of the first update's "
+                      f"{q} searches (random sample), search time scaled to all {q}; "
+                      f"build {t1 - t0:.2f} s, update {t2 - t1:.2f} s, sample {t4 - t3:.2f} s",
+            "evals_per_search": float(diag["evals"].mean())}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    net = workload(args.n)
+    threads = (os.cpu_count() or 1) if oracle.openmp_available() else 1
+    sample = 1 << 15
+    qi, qe = oracle.queries(net.vac_ax)
+    rng = np.random.default_rng(1)
+
+    def one(step):
+        sel = np.sort(rng.choice(len(qi), sample, replace=False))
+        t0 = time.perf_counter()
+        t = oracle.Tree(net.x, net.y, net.z)
+        t.reduce(net.vac_de)
+        t.search_batch(net.sigma, args.theta, net.seed, step, qi[sel], qe[sel], threads=threads)
+        return time.perf_counter() - t0
+
+    for w in range(args.warmup):
+        one(w)
+    secs = [one(args.warmup + k) for k in range(args.steps)]
+    tot = sum(secs)
+    value = sample * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(net, args.theta),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"per step: octree build + bottom-up update of the 2^20 "
+                                       f"network + {sample} random searches of it"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local if ws > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(device)
+    net = workload(args.n)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(net, args.theta)  # before any CUDA context-heavy work
+    run = Runner(net, args.theta, device)
+    prof = first_update_profile(run)
+    for _ in range(max(args.warmup, 3)):
+        run.step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = ClockSampler(device.index)
+    clocks.start()
+    res = run.timed(args.steps, e2e=False)
+    clk = clocks.stop()
+    if ws > 1:
+        dist.barrier()
+    units, secs = aggregate(res["searches"], res["ms"] / 1000.0, ws, device)
+    e2e = None
+    if not args.no_e2e:
+        run.step(e2e=True)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        r2 = run.timed(args.steps, e2e=True)
+        u2, s2 = aggregate(r2["searches"], r2["ms"] / 1000.0, ws, device)
+        e2e = {"value": u2 / s2, "unit": UNIT, "h2d_bytes_per_step": run.h2d_bytes(),
+               "d2h_bytes_per_step": run.d2h_bytes()}
+    if ws > 1:
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    pk, src = peaks()
+    clock_mhz = SM_MAX_MHZ
+    peak_tflops = SM_COUNT * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
+    flops = FLOPS_PER_EVAL * res["evals"]
+    achieved = flops / (res["kernel_ms"] / 1000.0) / 1e12 if res["kernel_ms"] > 0 else 0.0
+    roof = {"bound": "alu", "kernel": "bh_search_kernel", "achieved": achieved,
+            "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+            "traffic": None,
+            "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop/FMA x "
+                           f"{clock_mhz:.0f} MHz (FP32 pipe; MEASURED_PEAKS.json has only HBM and "
+                           f"bf16 peaks, {src})",
+            "work": f"{FLOPS_PER_EVAL} flop per node evaluation x {res['evals']} evaluations in "
+                    f"{res['kernel_launches']} launches",
+            "kernel_ms_per_launch": res["kernel_ms"] / max(res["kernel_launches"], 1),
+            "kernel_share_of_step": res["kernel_ms"] / res["ms"]}
+    line = {"metric": METRIC, "value": units / secs, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": res["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(net, args.theta, {
+                "parallelism": "replicas" if ws > 1 else "single GPU",
+                "searches_per_step": res["searches"] / args.steps,
+                "first_update": {"searches": prof["searches"], "formed": prof["formed"],
+                                 "ms_total": prof["ms_total"], "ms_reduce": prof["ms_reduce"],
+                                 "ms_search": prof["ms_search"],
+                                 "ms_search_kernel": prof["ms_search_kernel"],
+                                 "ms_accept": prof["ms_accept"], "ms_apply": prof["ms_apply"],
+                                 "searches_per_s": prof["searches"] / (prof["ms_total"] / 1e3)},
+                "evals_per_search": res["evals"] / max(res["searches"], 1)}),
+            "clocks": clk, "e2e": e2e, "gpu_launches": res["launches"],
+            "roofline": roof, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -66,6 +66,10 @@ typedef struct {
 /* Record per-search diagnostics (root-frontier ln S, node evaluations, restarts),
  * readable with relearn_get_search_diag. Costs a little extra memory traffic. */
 #define RELEARN_FLAG_DIAG 1u
+/* Record CUDA events around the phases of the update (stream-ordered, no
+ * synchronisation); read them later with relearn_get_last_stats and
+ * relearn_collect_search_times. */
+#define RELEARN_FLAG_TIMING 2u
 
 /* Host-side summary of one update (filled when a stats pointer is passed; this
  * synchronises the stream). Times are CUDA-event milliseconds. */
@@ -75,7 +79,14 @@ typedef struct {
     int64_t requests_declined; /* requests refused by over-requested targets */
     int64_t formed;            /* synapses formed */
     int64_t synapses;          /* synapses stored after the update */
-    float ms_reduce, ms_search, ms_accept, ms_apply, ms_total;
+    float ms_reduce;        /* bottom-up octree update */
+    float ms_search;        /* query setup + search kernel */
+    float ms_search_kernel; /* the search kernel alone */
+    float ms_accept, ms_apply, ms_total;
+    int32_t reserved;
+    int64_t searches_total;     /* searches of every update since the context was created */
+    int64_t evals_total;        /* node evaluations (count > 0) of those searches: the
+                                   algorithmic work of the search, one per frontier candidate */
 } relearn_update_stats;
 
 /* Create a context on CUDA device `device` that can hold up to max_neurons
@@ -190,6 +201,20 @@ relearn_status relearn_get_tree(relearn_ctx *ctx, int64_t capacity, int64_t *num
  * device uint32[4*count], key device uint32[2*count], out device uint32[4*count]. */
 relearn_status relearn_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out,
                                      int64_t count, void *stream);
+
+/* Counters and (when the update ran with RELEARN_FLAG_TIMING or a stats pointer) phase
+ * times of the last connectivity update. Synchronises the context's stream. Times are 0
+ * when no events were recorded. */
+relearn_status relearn_get_last_stats(relearn_ctx *ctx, relearn_update_stats *stats);
+
+/* Sum of the search-kernel durations (CUDA events, ms) of the updates run with
+ * RELEARN_FLAG_TIMING since the previous call (up to 64), and how many there were.
+ * Synchronises the context's stream; resets the record. Host pointers. */
+relearn_status relearn_collect_search_times(relearn_ctx *ctx, double *total_ms, int64_t *launches);
+
+/* Total number of CUDA kernels this library has launched in the process (all contexts).
+ * `count` is a host pointer. Never fails for a non-NULL pointer. */
+relearn_status relearn_launch_count(int64_t *count);
 
 /* Synchronise the context's last stream, fold the device status word into the result and
  * return it; *msg (host, may be NULL) points at a static description of the last error.

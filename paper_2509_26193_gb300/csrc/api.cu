@@ -1,6 +1,7 @@
 // C ABI of librelearn (declared in include/relearn.h): argument checks,
 // context allocation, and the order of the kernels of each call.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -9,6 +10,12 @@
 #include "internal.h"
 
 using namespace rl;
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+} // namespace
+
+void rl::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 namespace {
 
@@ -92,6 +99,12 @@ void free_all(relearn_ctx *c)
             cudaEventDestroy(ev);
             ev = nullptr;
         }
+    for (auto &pair : c->kev)
+        for (cudaEvent_t &ev : pair)
+            if (ev) {
+                cudaEventDestroy(ev);
+                ev = nullptr;
+            }
 }
 
 bool params_ok(const relearn_params *p)
@@ -222,6 +235,9 @@ relearn_status relearn_create(relearn_ctx **out, int device, int64_t max_neurons
         c->sort.scan = c->scan;
         for (cudaEvent_t &ev : c->ev)
             if (e == cudaSuccess) e = cudaEventCreate(&ev);
+        for (auto &pair : c->kev)
+            for (cudaEvent_t &ev : pair)
+                if (e == cudaSuccess) e = cudaEventCreate(&ev);
     }
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->d_i64, 0, 16 * sizeof(int64_t));
@@ -294,34 +310,25 @@ relearn_status relearn_update_connectivity(relearn_ctx *c, const relearn_params 
     if (!g.ok) return fail(c, RELEARN_ERR_CUDA, "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
     c->last_stream = st;
-    if (stats) CK(cudaEventRecord(c->ev[0], st), "event");
+    const bool timed = stats || (p->flags & RELEARN_FLAG_TIMING);
+    c->timed = timed;
+    if (timed) CK(cudaEventRecord(c->ev[0], st), "event");
     CK(octree_reduce(c, vac_de, st), "reduce");
-    if (stats) CK(cudaEventRecord(c->ev[1], st), "event");
+    if (timed) CK(cudaEventRecord(c->ev[1], st), "event");
     CK(search_prepare(c, *p, vac_ax, st), "search prepare");
+    if (timed) CK(cudaEventRecord(c->ev[2], st), "event");
+    const bool ring = (p->flags & RELEARN_FLAG_TIMING) && c->nkev < 64;
+    if (ring) CK(cudaEventRecord(c->kev[c->nkev][0], st), "event");
     CK(search_run(c, *p, st), "search");
-    if (stats) CK(cudaEventRecord(c->ev[2], st), "event");
+    if (ring) CK(cudaEventRecord(c->kev[c->nkev++][1], st), "event");
+    if (timed) CK(cudaEventRecord(c->ev[3], st), "event");
     CK(accept_requests(c, *p, vac_de, st), "accept");
-    if (stats) CK(cudaEventRecord(c->ev[3], st), "event");
+    if (timed) CK(cudaEventRecord(c->ev[4], st), "event");
     CK(apply_requests(c, vac_ax, vac_de, type, st), "apply");
-    if (stats) CK(cudaEventRecord(c->ev[4], st), "event");
+    if (timed) CK(cudaEventRecord(c->ev[5], st), "event");
     c->diag_valid = (p->flags & RELEARN_FLAG_DIAG) != 0;
-    if (stats) {
-        relearn_status s = sync(c);
-        int64_t h[16];
-        CK(cudaMemcpy(h, c->d_i64, sizeof(h), cudaMemcpyDeviceToHost), "stats copy");
-        memset(stats, 0, sizeof(*stats));
-        stats->searches = h[I64_Q];
-        stats->failed = h[I64_FAILED];
-        stats->requests_declined = h[I64_DECLINED];
-        stats->formed = h[I64_FORMED];
-        stats->synapses = h[I64_NSYN];
-        cudaEventElapsedTime(&stats->ms_reduce, c->ev[0], c->ev[1]);
-        cudaEventElapsedTime(&stats->ms_search, c->ev[1], c->ev[2]);
-        cudaEventElapsedTime(&stats->ms_accept, c->ev[2], c->ev[3]);
-        cudaEventElapsedTime(&stats->ms_apply, c->ev[3], c->ev[4]);
-        cudaEventElapsedTime(&stats->ms_total, c->ev[0], c->ev[4]);
-        return s;
-    }
+    c->stats_valid = true;
+    if (stats) return relearn_get_last_stats(c, stats);
     return RELEARN_OK;
 }
 
@@ -519,7 +526,59 @@ relearn_status relearn_philox4x32_10(const uint32_t *ctr, const uint32_t *key, u
     int64_t blocks = (count + 255) / 256;
     if (blocks > 65535) blocks = 65535;
     philox_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(ctr, key, out, count);
+    note_launch();
     return cudaGetLastError() == cudaSuccess ? RELEARN_OK : RELEARN_ERR_CUDA;
+}
+
+relearn_status relearn_get_last_stats(relearn_ctx *c, relearn_update_stats *stats)
+{
+    if (!c || !stats) return RELEARN_ERR_INVALID_ARG;
+    if (!c->stats_valid) return fail(c, RELEARN_ERR_STATE, "no connectivity update has run");
+    DeviceGuard g(c->device);
+    relearn_status s = sync(c);
+    int64_t h[16];
+    CK(cudaMemcpy(h, c->d_i64, sizeof(h), cudaMemcpyDeviceToHost), "stats copy");
+    memset(stats, 0, sizeof(*stats));
+    stats->searches = h[I64_Q];
+    stats->failed = h[I64_FAILED];
+    stats->requests_declined = h[I64_DECLINED];
+    stats->formed = h[I64_FORMED];
+    stats->synapses = h[I64_NSYN];
+    stats->searches_total = h[I64_Q_TOTAL];
+    stats->evals_total = h[I64_EVALS_TOTAL];
+    if (c->timed) {
+        cudaEventElapsedTime(&stats->ms_reduce, c->ev[0], c->ev[1]);
+        cudaEventElapsedTime(&stats->ms_search, c->ev[1], c->ev[3]);
+        cudaEventElapsedTime(&stats->ms_search_kernel, c->ev[2], c->ev[3]);
+        cudaEventElapsedTime(&stats->ms_accept, c->ev[3], c->ev[4]);
+        cudaEventElapsedTime(&stats->ms_apply, c->ev[4], c->ev[5]);
+        cudaEventElapsedTime(&stats->ms_total, c->ev[0], c->ev[5]);
+    }
+    return s;
+}
+
+relearn_status relearn_collect_search_times(relearn_ctx *c, double *total_ms, int64_t *launches)
+{
+    if (!c || !total_ms || !launches) return RELEARN_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    relearn_status s = sync(c);
+    double tot = 0.0;
+    for (int k = 0; k < c->nkev; ++k) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, c->kev[k][0], c->kev[k][1]), "event time");
+        tot += ms;
+    }
+    *total_ms = tot;
+    *launches = c->nkev;
+    c->nkev = 0;
+    return s;
+}
+
+relearn_status relearn_launch_count(int64_t *count)
+{
+    if (!count) return RELEARN_ERR_INVALID_ARG;
+    *count = g_launches.load(std::memory_order_relaxed);
+    return RELEARN_OK;
 }
 
 relearn_status relearn_last_error(relearn_ctx *c, const char **msg)

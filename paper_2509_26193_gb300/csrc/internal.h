@@ -101,15 +101,23 @@ struct relearn_ctx {
     rl::SortScratch sort;
 
     cudaEvent_t ev[8] = {};
+    bool timed = false; // the last update recorded its phase events
+    cudaEvent_t kev[64][2] = {}; // search-kernel start/stop of timed updates
+    int nkev = 0;
     bool diag_valid = false;
+    bool stats_valid = false;
 };
 
 // slots of d_i64 / d_i32
 enum { I64_Q = 0, I64_FAILED, I64_DECLINED, I64_FORMED, I64_NSYN, I64_BROKEN, I64_SCAN_TOTAL,
-       I64_NODES };
+       I64_NODES, I64_Q_TOTAL, I64_EVALS_TOTAL };
 enum { I32_N = 0, I32_Q, I32_NSYN, I32_NEW, I32_NODES, I32_WORK };
 
 namespace rl {
+
+// api.cu --------------------------------------------------------------------
+// Counts kernel launches made by the library (reported by relearn_launch_count).
+void note_launch();
 
 // scan.cu -------------------------------------------------------------------
 // out[i] = sum(in[0 .. i)) for i < count; *total = sum(in[0 .. count)) (int64).

@@ -353,11 +353,15 @@ cudaError_t octree_build(relearn_ctx *c, int64_t n, const float *x, const float 
     uint32_t *ord = reinterpret_cast<uint32_t *>(c->d_cnt); // 6 words of scratch
     if (!box.given) {
         bbox_init_kernel<<<1, 32, 0, st>>>(ord);
+        note_launch();
         bbox_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(x, y, z, n, ord);
+        note_launch();
     }
     geom_kernel<<<1, 1, 0, st>>>(ord, box, c->d_geom);
+    note_launch();
     morton_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(x, y, z, n, c->d_geom,
                                                                   c->d_codes, c->d_perm);
+    note_launch();
     int which = 0;
     if ((e = radix_sort_u32(c->d_codes, c->d_codes_alt, c->d_perm, c->d_perm_alt, n, nullptr, 30,
                             c->sort, st, &which)))
@@ -372,15 +376,19 @@ cudaError_t octree_build(relearn_ctx *c, int64_t n, const float *x, const float 
     }
     gather_pos_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(x, y, z, c->d_perm, n,
                                                                       c->d_pos);
+    note_launch();
     if ((e = cudaMemsetAsync(c->d_mask, 0, n * sizeof(uint32_t), st))) return e;
     topo_pairs_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(c->d_codes, n, c->d_mask);
+    note_launch();
     topo_count_kernel<<<grid_for(n + 1, 256, c->num_sms), 256, 0, st>>>(c->d_mask, n, c->d_cnt);
+    note_launch();
     if ((e = scan_exclusive(c->d_cnt, c->d_base, n + 1, nullptr, c->d_i64 + I64_NODES, c->scan,
                             st)))
         return e;
     if ((e = cudaMemsetAsync(c->d_nchild, 0, c->max_nodes * sizeof(int32_t), st))) return e;
     topo_emit_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(
         c->d_codes, n, c->d_mask, c->d_base, c->d_nodes, c->d_parent, c->d_nchild, c->d_leaf);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -391,6 +399,7 @@ cudaError_t octree_reduce(relearn_ctx *c, const int32_t *vac_de, cudaStream_t st
     reduce_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(
         c->d_nodes, c->d_parent, c->d_nchild, c->d_arrive, c->d_acc, c->d_leaf, c->d_perm,
         c->d_pos, vac_de, c->n);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -137,8 +137,11 @@ cudaError_t scan_exclusive(const int32_t *in, int32_t *out, int64_t max_n, const
     if (nb == 0) nb = 1;
     if (nb > s.max_blocks) return cudaErrorInvalidValue;
     scan_reduce_kernel<<<(unsigned)nb, kThreads, 0, st>>>(in, max_n, d_count, s.block_sums);
+    note_launch();
     scan_spine_kernel<<<1, 1024, 0, st>>>(s.block_sums, nb, d_total);
+    note_launch();
     scan_down_kernel<<<(unsigned)nb, kThreads, 0, st>>>(in, out, max_n, d_count, s.block_sums);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -148,6 +151,7 @@ cudaError_t fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t st)
     int64_t blocks = (n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     fill_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, v, n);
+    note_launch();
     return cudaGetLastError();
 }
 

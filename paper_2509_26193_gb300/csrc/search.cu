@@ -53,7 +53,7 @@ __global__ void query_counts_kernel(const int32_t *__restrict__ vac_ax,
 
 // Q = total; beyond capacity the update is void (status CAPACITY, Q = 0).
 __global__ void query_check_kernel(const int64_t *d_total, int64_t max_searches, int32_t *d_Q,
-                                   int64_t *d_Qout, int32_t *status)
+                                   int64_t *d_Qout, int64_t *d_Qsum, int32_t *status)
 {
     int64_t q = *d_total;
     *d_Qout = q;
@@ -62,6 +62,7 @@ __global__ void query_check_kernel(const int64_t *d_total, int64_t max_searches,
         q = 0;
     }
     *d_Q = (int32_t)q;
+    *d_Qsum += q;
 }
 
 __global__ void query_fill_kernel(const int32_t *__restrict__ vac_ax,
@@ -99,6 +100,7 @@ struct SearchArgs {
     int32_t *work;
     int32_t *req_tgt;
     int64_t *failed;
+    int64_t *evals_total;
     double *diag_lns;
     int32_t *diag_evals;
     int32_t *diag_restarts;
@@ -162,6 +164,7 @@ __global__ void __launch_bounds__(256) bh_search_kernel(SearchArgs a)
     const float k2 = s_k2;
     const int32_t Q = *a.d_Q;
     const int lane = threadIdx.x & 31;
+    int64_t warp_evals = 0; // node evaluations of this lane's searches
     for (;;) {
         int32_t qb = 0;
         if (lane == 0) qb = atomicAdd(a.work, 32);
@@ -203,6 +206,7 @@ __global__ void __launch_bounds__(256) bh_search_kernel(SearchArgs a)
             sdepth = tk.y & 15;
         }
         const int32_t slot = a.qoff_o[i] + e;
+        warp_evals += evals;
         a.req_tgt[slot] = result;
         if (result < 0) atomicAdd(reinterpret_cast<unsigned long long *>(a.failed), 1ull);
         if (a.diag_lns) {
@@ -211,6 +215,10 @@ __global__ void __launch_bounds__(256) bh_search_kernel(SearchArgs a)
             a.diag_restarts[slot] = draws > 0 ? draws - 1 : 0;
         }
     }
+    for (int off = 16; off; off >>= 1) warp_evals += __shfl_xor_sync(0xffffffffu, warp_evals, off);
+    if (lane == 0 && warp_evals)
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.evals_total),
+                  (unsigned long long)warp_evals);
 }
 
 inline unsigned grid_for(int64_t n, int threads, int num_sms)
@@ -230,18 +238,23 @@ cudaError_t search_prepare(relearn_ctx *c, const relearn_params &p, const int32_
     cudaError_t e;
     const int64_t n = c->n;
     search_const_kernel<<<1, 1, 0, st>>>(c->d_geom, p.sigma, p.theta, c->d_sc);
+    note_launch();
     int32_t *cnt_s = c->d_cnt, *cnt_o = c->d_tcnt; // scratch
     query_counts_kernel<<<grid_for(n + 1, 256, c->num_sms), 256, 0, st>>>(vac_ax, c->d_perm, n,
                                                                           cnt_s, cnt_o);
+    note_launch();
     if ((e = scan_exclusive(cnt_s, c->d_qoff_s, n + 1, nullptr, c->d_i64 + I64_SCAN_TOTAL,
                             c->scan, st)))
         return e;
     if ((e = scan_exclusive(cnt_o, c->d_qoff_o, n + 1, nullptr, nullptr, c->scan, st))) return e;
     query_check_kernel<<<1, 1, 0, st>>>(c->d_i64 + I64_SCAN_TOTAL, c->max_searches,
-                                        c->d_i32 + I32_Q, c->d_i64 + I64_Q, c->d_status);
+                                        c->d_i32 + I32_Q, c->d_i64 + I64_Q,
+                                        c->d_i64 + I64_Q_TOTAL, c->d_status);
+    note_launch();
     query_fill_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(
         vac_ax, c->d_perm, n, c->d_qoff_s, c->d_qoff_o, c->d_i32 + I32_Q, c->d_qsrc,
         c->d_req_src, c->d_req_elem, c->d_req_tgt);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -262,6 +275,7 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, cudaStream_t st)
     a.work = c->d_i32 + I32_WORK;
     a.req_tgt = c->d_req_tgt;
     a.failed = c->d_i64 + I64_FAILED;
+    a.evals_total = c->d_i64 + I64_EVALS_TOTAL;
     const bool diag = (p.flags & RELEARN_FLAG_DIAG) != 0;
     a.diag_lns = diag ? c->d_diag_lns : nullptr;
     a.diag_evals = diag ? c->d_diag_evals : nullptr;
@@ -273,6 +287,7 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, cudaStream_t st)
         return e;
     if (per_sm < 1) per_sm = 1;
     bh_search_kernel<<<c->num_sms * per_sm, 256, 0, st>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 

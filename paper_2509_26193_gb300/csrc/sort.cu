@@ -117,11 +117,13 @@ cudaError_t radix_sort(K *keys, K *keys_alt, int32_t *vals, int32_t *vals_alt, i
     int32_t *vin = vals, *vout = vals_alt;
     for (int shift = 0; shift < end_bit; shift += 8) {
         hist_kernel<K><<<nb, kThreads, 0, st>>>(kin, max_n, d_count, shift, s.hist, nb);
+        note_launch();
         cudaError_t e = scan_exclusive(s.hist, s.hist, (int64_t)kRadix * nb, nullptr, nullptr,
                                        s.scan, st);
         if (e != cudaSuccess) return e;
         scatter_kernel<K><<<nb, kThreads, 0, st>>>(kin, vin, kout, vout, max_n, d_count, shift,
                                                     s.hist, nb);
+        note_launch();
         K *tk = kin;
         kin = kout;
         kout = tk;

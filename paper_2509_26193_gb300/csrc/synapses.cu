@@ -370,12 +370,15 @@ cudaError_t accept_requests(relearn_ctx *c, const relearn_params &p, const int32
     if ((e = cudaMemsetAsync(c->d_i64 + I64_DECLINED, 0, sizeof(int64_t), st))) return e;
     accept_count_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_src, c->d_req_elem, c->d_req_tgt,
                                             c->d_req_prio, c->d_tcnt, p.seed, (uint32_t)p.step);
+    note_launch();
     if ((e = scan_exclusive(c->d_tcnt, c->d_toff, n + 1, nullptr, nullptr, c->scan, st))) return e;
     accept_scatter_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_tgt, c->d_toff, c->d_tfill,
                                               c->d_bucket);
+    note_launch();
     accept_decide_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_src, c->d_req_elem, c->d_req_tgt,
                                              c->d_req_prio, c->d_tcnt, c->d_toff, c->d_bucket,
                                              vac_de, c->d_req_acc, c->d_i64 + I64_DECLINED);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -387,6 +390,7 @@ cudaError_t canonicalise_store(relearn_ctx *c, cudaStream_t st)
     const unsigned gs = grid_for(c->max_synapses, 256, c->num_sms);
     make_keys_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_syn_tgt, c->d_syn_sign, bits,
                                          c->d_key, c->d_val);
+    note_launch();
     int which = 0;
     if ((e = radix_sort_u64(c->d_key, c->d_key_alt, c->d_val, c->d_val_alt, c->max_synapses, dm,
                             2 * bits, c->sort, st, &which)))
@@ -394,6 +398,7 @@ cudaError_t canonicalise_store(relearn_ctx *c, cudaStream_t st)
     unpack_keys_kernel<<<gs, 256, 0, st>>>(dm, which ? c->d_key_alt : c->d_key,
                                            which ? c->d_val_alt : c->d_val, bits, c->d_syn_src,
                                            c->d_syn_tgt, c->d_syn_sign);
+    note_launch();
     return rebuild_views(c, st);
 }
 
@@ -409,6 +414,7 @@ cudaError_t rebuild_views(relearn_ctx *c, cudaStream_t st)
     if ((e = cudaMemsetAsync(in_cnt, 0, (n + 1) * sizeof(int32_t), st))) return e;
     degree_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_syn_tgt, out_cnt, in_cnt, c->d_key32,
                                       c->d_val);
+    note_launch();
     if ((e = scan_exclusive(out_cnt, c->d_out_ptr, n + 1, nullptr, nullptr, c->scan, st)))
         return e;
     if ((e = scan_exclusive(in_cnt, c->d_in_ptr, n + 1, nullptr, nullptr, c->scan, st))) return e;
@@ -418,6 +424,7 @@ cudaError_t rebuild_views(relearn_ctx *c, cudaStream_t st)
         return e;
     in_view_kernel<<<gs, 256, 0, st>>>(dm, which ? c->d_val_alt : c->d_val, c->d_syn_src,
                                        c->d_syn_sign, c->d_in_syn, c->d_in_src, c->d_in_sign);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -428,17 +435,21 @@ cudaError_t apply_requests(relearn_ctx *c, int32_t *vac_ax, int32_t *vac_de, con
     const int32_t *dQ = c->d_i32 + I32_Q;
     const unsigned gq = grid_for(c->max_searches, 256, c->num_sms);
     flags_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_acc, c->d_newpos);
+    note_launch();
     if ((e = scan_exclusive(c->d_newpos, c->d_newpos, c->max_searches, dQ,
                             c->d_i64 + I64_SCAN_TOTAL, c->scan, st)))
         return e;
     apply_check_kernel<<<1, 1, 0, st>>>(c->d_i64 + I64_SCAN_TOTAL, c->d_i32 + I32_NSYN,
                                         c->d_i32 + I32_NEW, c->max_synapses, c->d_status,
                                         c->d_i64 + I64_FORMED);
+    note_launch();
     apply_kernel<<<gq, 256, 0, st>>>(dQ, c->d_i32 + I32_NEW, c->d_i32 + I32_NSYN, c->d_req_src,
                                      c->d_req_tgt, c->d_req_acc, c->d_newpos, type, vac_ax,
                                      vac_de, c->d_syn_src, c->d_syn_tgt, c->d_syn_sign);
+    note_launch();
     grow_store_kernel<<<1, 1, 0, st>>>(c->d_i32 + I32_NEW, c->d_i32 + I32_NSYN,
                                        c->d_i64 + I64_NSYN);
+    note_launch();
     return canonicalise_store(c, st);
 }
 
@@ -455,24 +466,32 @@ cudaError_t delete_synapses(relearn_ctx *c, const relearn_params &p, const int32
     delete_needs_kernel<<<gn, 256, 0, st>>>(n, retract_ax, retract_de, vac_ax, vac_de,
                                             c->d_out_ptr, c->d_in_ptr, c->d_need_ax,
                                             c->d_need_de);
+    note_launch();
     delete_prio_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_in_syn, c->d_syn_tgt,
                                            c->d_out_ptr, c->d_in_ptr, c->d_prio_ax, c->d_prio_de,
                                            c->d_sel_ax, c->d_sel_de, p.seed, (uint32_t)p.step);
+    note_launch();
     delete_select_kernel<<<gn, 256, 0, st>>>(n, c->d_out_ptr, c->d_need_ax, c->d_prio_ax, nullptr,
                                              c->d_sel_ax);
+    note_launch();
     delete_select_kernel<<<gn, 256, 0, st>>>(n, c->d_in_ptr, c->d_need_de, c->d_prio_de,
                                              c->d_in_syn, c->d_sel_de);
+    note_launch();
     delete_apply_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_syn_tgt, c->d_sel_ax,
                                             c->d_sel_de, vac_ax, vac_de, c->d_keep);
+    note_launch();
     if ((e = scan_exclusive(c->d_keep, c->d_keep, c->max_synapses, dm, c->d_i64 + I64_SCAN_TOTAL,
                             c->scan, st)))
         return e;
     compact_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_syn_tgt, c->d_syn_sign, c->d_sel_ax,
                                        c->d_sel_de, c->d_keep, bits, c->d_key, c->d_val);
+    note_launch();
     shrink_store_kernel<<<1, 1, 0, st>>>(c->d_i32 + I32_NSYN, c->d_i64 + I64_SCAN_TOTAL,
                                          c->d_i64 + I64_BROKEN, c->d_i64 + I64_NSYN);
+    note_launch();
     unpack_keys_kernel<<<gs, 256, 0, st>>>(dm, c->d_key, c->d_val, bits, c->d_syn_src,
                                            c->d_syn_tgt, c->d_syn_sign);
+    note_launch();
     return rebuild_views(c, st);
 }
 
@@ -481,6 +500,7 @@ cudaError_t deliver_spikes(relearn_ctx *c, const uint8_t *spiked, int32_t *input
 {
     spikes_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(
         c->n, c->d_in_ptr, c->d_in_src, c->d_in_sign, spiked, input);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_CAPACITY, ERR_TIMEOUT, ERR_STATE = r
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CAPACITY", 5: "TIMEOUT",
                 6: "STATE"}
 FLAG_DIAG = 1
+FLAG_TIMING = 2
 
 _lock = threading.Lock()
 _lib = None
@@ -44,8 +45,10 @@ class relearn_update_stats(ctypes.Structure):
     _fields_ = [("searches", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("requests_declined", ctypes.c_int64), ("formed", ctypes.c_int64),
                 ("synapses", ctypes.c_int64), ("ms_reduce", ctypes.c_float),
-                ("ms_search", ctypes.c_float), ("ms_accept", ctypes.c_float),
-                ("ms_apply", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_search", ctypes.c_float), ("ms_search_kernel", ctypes.c_float),
+                ("ms_accept", ctypes.c_float), ("ms_apply", ctypes.c_float),
+                ("ms_total", ctypes.c_float), ("reserved", ctypes.c_int32),
+                ("searches_total", ctypes.c_int64), ("evals_total", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -68,6 +71,9 @@ _SIGS = {
     "relearn_get_search_diag": [_P, _I64, ctypes.POINTER(_I64), _P, _P, _P],
     "relearn_get_tree": [_P, _I64, ctypes.POINTER(_I64)] + [_P] * 10,
     "relearn_philox4x32_10": [_P, _P, _P, _I64, _P],
+    "relearn_get_last_stats": [_P, ctypes.POINTER(relearn_update_stats)],
+    "relearn_collect_search_times": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)],
+    "relearn_launch_count": [ctypes.POINTER(_I64)],
     "relearn_last_error": [_P, ctypes.POINTER(ctypes.c_char_p)],
 }
 
@@ -313,6 +319,28 @@ def relearn_philox4x32_10(ctr, key, out, stream=None):
     o = _dev_ptr(out, torch.int32, 4 * n, "out")
     st = lib().relearn_philox4x32_10(c, k, o, n, _stream(stream))
     _raise(None, st, "relearn_philox4x32_10")
+
+
+def relearn_get_last_stats(ctx):
+    s = relearn_update_stats()
+    st = lib().relearn_get_last_stats(ctx.handle, ctypes.byref(s))
+    _raise(ctx, st, "relearn_get_last_stats")
+    return s.as_dict()
+
+
+def relearn_collect_search_times(ctx):
+    ms = ctypes.c_double(0.0)
+    k = ctypes.c_int64(0)
+    st = lib().relearn_collect_search_times(ctx.handle, ctypes.byref(ms), ctypes.byref(k))
+    _raise(ctx, st, "relearn_collect_search_times")
+    return ms.value, k.value
+
+
+def relearn_launch_count():
+    c = ctypes.c_int64(0)
+    st = lib().relearn_launch_count(ctypes.byref(c))
+    _raise(None, st, "relearn_launch_count")
+    return c.value
 
 
 def relearn_last_error(ctx):

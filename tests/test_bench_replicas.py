@@ -1,0 +1,51 @@
+"""The N > 1 path is replicas only (each rank runs its own network, no data-path
+collective); bench.aggregate combines the ranks: units summed, time = slowest
+rank. Checked with world_size 2 over gloo on CPU."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ws, r, local = bench.dist_env()
+    assert (ws, r, local) == (world, rank, rank)
+    units, secs = bench.aggregate(1000.0 * (rank + 1), 0.5 + rank, ws)
+    out.put((rank, units, secs))
+    dist.destroy_process_group()
+
+
+def test_aggregate_two_ranks_gloo():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(world))
+    for rank, units, secs in res:
+        assert units == pytest.approx(3000.0)   # 1000 + 2000: whole-job searches
+        assert secs == pytest.approx(1.5)       # slowest rank
+
+
+def test_single_rank_passthrough():
+    import bench
+    assert bench.aggregate(123.0, 0.25, 1) == (123.0, 0.25)
