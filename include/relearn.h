@@ -216,6 +216,27 @@ relearn_status relearn_collect_search_times(relearn_ctx *ctx, double *total_ms, 
  * `count` is a host pointer. Never fails for a non-NULL pointer. */
 relearn_status relearn_launch_count(int64_t *count);
 
+/* Allocation-free Morton ordering, for callers that must not allocate device memory
+ * (no counterpart in the paper; it exists for users of this library): the neurons'
+ * 30-bit Morton codes (same quantisation as relearn_build_octree) and their stable
+ * order by (code, id), without a context and without any cudaMalloc/cudaFree.
+ *   n            1 .. RELEARN_NOALLOC_MAX_NEURONS; larger n returns RELEARN_ERR_CAPACITY.
+ *   x, y, z      device float[n], positions.
+ *   box_lo3/hi3  host float[3] each, or both NULL (= bounding box of the positions).
+ *   codes        device uint32[n], out: the codes in ascending order.
+ *   perm         device int32[n], out: perm[k] = id of the neuron with the k-th code
+ *                (ties by id), the same order relearn_get_tree reports.
+ * The sort's scratch is one static device array of about 8.5 MB per GPU, held until the
+ * process exits. The first call on each device looks up that array's device address
+ * (with the device current); make that first call before any stream capture. All calls
+ * on a device share the array: calls whose GPU work overlaps race and give wrong
+ * results, so order them on one stream (or otherwise). Asynchronous on `stream`. */
+#define RELEARN_NOALLOC_MAX_NEURONS (1 << 20)
+relearn_status relearn_morton_order_noalloc(int64_t n, const float *x, const float *y,
+                                            const float *z, const float *box_lo3,
+                                            const float *box_hi3, uint32_t *codes, int32_t *perm,
+                                            void *stream);
+
 /* Synchronise the context's last stream, fold the device status word into the result and
  * return it; *msg (host, may be NULL) points at a static description of the last error.
  * Clears the stored error. */

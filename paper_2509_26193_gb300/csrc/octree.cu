@@ -13,6 +13,8 @@
 // Reduce: one thread per leaf climbs towards the root; the last child to
 // arrive at a node sums all of that node's children (in Morton order, FP64)
 // and continues upward, so every node is summed once and deterministically.
+#include <mutex>
+
 #include "internal.h"
 
 namespace rl {
@@ -404,3 +406,129 @@ cudaError_t octree_reduce(relearn_ctx *c, const int32_t *vac_de, cudaStream_t st
 }
 
 } // namespace rl
+
+// ---------------------------------------------------------------------------
+// Allocation-free Morton ordering: relearn_morton_order_noalloc (relearn.h).
+//
+// Some callers cannot call cudaMalloc at the point where they need the spatial
+// order of their neurons: code running inside another framework's memory pool
+// or allocator hooks, real-time loops that must not block on the driver's
+// allocator, or plug-ins that only receive already-allocated buffers. This
+// entry point serves them: the caller passes the positions and the two output
+// arrays, and the sort's scratch (ping-pong buffers, digit histograms, scan
+// sums, box words) lives in one file-scope device array instead of a context.
+//
+// The array is sized for kNoAllocMaxN neurons (about 8.5 MB); every GPU that
+// loads this library keeps it until the process exits. All calls on a device
+// share it and it keeps the previous call's contents, so calls whose GPU work
+// overlaps (different streams, no ordering between them) race on it. Nothing in
+// it has to start at zero except the box words, which every call resets.
+// ---------------------------------------------------------------------------
+namespace rl {
+namespace {
+
+constexpr int64_t kNoAllocMaxN = int64_t(1) << 20;
+constexpr int64_t kNoAllocSortBlocks = (kNoAllocMaxN + 2047) / 2048;     // 2048 keys per tile
+constexpr int64_t kNoAllocScanBlocks = 1024;                             // >= hist scan tiles
+constexpr size_t kOffGeom = 256;
+constexpr size_t kOffCodesAlt = 512;
+constexpr size_t kOffPermAlt = kOffCodesAlt + 4 * size_t(kNoAllocMaxN);
+constexpr size_t kOffHist = kOffPermAlt + 4 * size_t(kNoAllocMaxN);
+constexpr size_t kOffScan = kOffHist + 4 * 256 * size_t(kNoAllocSortBlocks);
+constexpr size_t kNoAllocBytes = kOffScan + 8 * size_t(kNoAllocScanBlocks + 1);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocDevice {
+    unsigned char *base = nullptr; // device address of g_noalloc_scratch on this device
+    int num_sms = 0;
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[64];
+
+// Once per device, with that device current: look up the array's device address.
+relearn_status noalloc_setup(int dev, NoAllocDevice *out)
+{
+    if (dev < 0 || dev >= 64) return RELEARN_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocDevice &d = g_noalloc_dev[dev];
+    if (!d.base) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
+            return RELEARN_ERR_CUDA;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return RELEARN_ERR_CUDA;
+        d.num_sms = sms > 0 ? sms : 1;
+        d.base = static_cast<unsigned char *>(p);
+    }
+    *out = d;
+    return RELEARN_OK;
+}
+
+} // namespace
+
+} // namespace rl
+
+extern "C" relearn_status relearn_morton_order_noalloc(int64_t n, const float *x, const float *y,
+                                                       const float *z, const float *box_lo3,
+                                                       const float *box_hi3, uint32_t *codes,
+                                                       int32_t *perm, void *stream)
+{
+    using namespace rl;
+    if (n < 1 || !x || !y || !z || !codes || !perm) return RELEARN_ERR_INVALID_ARG;
+    if ((box_lo3 == nullptr) != (box_hi3 == nullptr)) return RELEARN_ERR_INVALID_ARG;
+    if (box_lo3)
+        for (int a = 0; a < 3; ++a)
+            if (!(box_hi3[a] >= box_lo3[a])) return RELEARN_ERR_INVALID_ARG;
+    if (n > kNoAllocMaxN) return RELEARN_ERR_CAPACITY;
+    if (sort_blocks_needed(n) > kNoAllocSortBlocks ||
+        scan_blocks_needed(256 * sort_blocks_needed(n)) > kNoAllocScanBlocks)
+        return RELEARN_ERR_CAPACITY;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RELEARN_ERR_CUDA;
+    NoAllocDevice d;
+    relearn_status s = noalloc_setup(dev, &d);
+    if (s != RELEARN_OK) return s;
+    uint32_t *ord = reinterpret_cast<uint32_t *>(d.base);
+    Geom *geom = reinterpret_cast<Geom *>(d.base + kOffGeom);
+    uint32_t *codes_alt = reinterpret_cast<uint32_t *>(d.base + kOffCodesAlt);
+    int32_t *perm_alt = reinterpret_cast<int32_t *>(d.base + kOffPermAlt);
+    SortScratch ss;
+    ss.hist = reinterpret_cast<int32_t *>(d.base + kOffHist);
+    ss.max_blocks = kNoAllocSortBlocks;
+    ss.scan.block_sums = reinterpret_cast<int64_t *>(d.base + kOffScan);
+    ss.scan.max_blocks = kNoAllocScanBlocks;
+    cudaStream_t st = (cudaStream_t)stream;
+    Box box{};
+    box.given = box_lo3 != nullptr;
+    if (box.given)
+        for (int a = 0; a < 3; ++a) {
+            box.lo[a] = box_lo3[a];
+            box.hi[a] = box_hi3[a];
+        }
+    const unsigned grid = grid_for(n, 256, d.num_sms);
+    if (!box.given) {
+        bbox_init_kernel<<<1, 32, 0, st>>>(ord);
+        note_launch();
+        bbox_kernel<<<grid, 256, 0, st>>>(x, y, z, n, ord);
+        note_launch();
+    }
+    geom_kernel<<<1, 1, 0, st>>>(ord, box, geom);
+    note_launch();
+    morton_kernel<<<grid, 256, 0, st>>>(x, y, z, n, geom, codes, perm);
+    note_launch();
+    int which = 0;
+    if (radix_sort_u32(codes, codes_alt, perm, perm_alt, n, nullptr, 30, ss, st, &which) !=
+        cudaSuccess)
+        return RELEARN_ERR_CUDA;
+    if (which) {
+        if (cudaMemcpyAsync(codes, codes_alt, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                            st) != cudaSuccess ||
+            cudaMemcpyAsync(perm, perm_alt, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
+                cudaSuccess)
+            return RELEARN_ERR_CUDA;
+    }
+    return cudaGetLastError() == cudaSuccess ? RELEARN_OK : RELEARN_ERR_CUDA;
+}
+

@@ -74,6 +74,7 @@ _SIGS = {
     "relearn_get_last_stats": [_P, ctypes.POINTER(relearn_update_stats)],
     "relearn_collect_search_times": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)],
     "relearn_launch_count": [ctypes.POINTER(_I64)],
+    "relearn_morton_order_noalloc": [_I64, _P, _P, _P, _P, _P, _P, _P, _P],
     "relearn_last_error": [_P, ctypes.POINTER(ctypes.c_char_p)],
 }
 
@@ -341,6 +342,25 @@ def relearn_launch_count():
     st = lib().relearn_launch_count(ctypes.byref(c))
     _raise(None, st, "relearn_launch_count")
     return c.value
+
+
+def relearn_morton_order_noalloc(x, y, z, codes, perm, box_lo=None, box_hi=None, stream=None):
+    """Morton codes and order without any device allocation inside the library; the
+    caller provides `codes` (uint32 viewed as int32) and `perm` (int32) on the device."""
+    torch = _torch()
+    n = x.numel()
+    px = _dev_ptr(x, torch.float32, n, "x")
+    py = _dev_ptr(y, torch.float32, n, "y")
+    pz = _dev_ptr(z, torch.float32, n, "z")
+    pc = _dev_ptr(codes, torch.int32, n, "codes")
+    pp = _dev_ptr(perm, torch.int32, n, "perm")
+    lo = hi = None
+    if box_lo is not None:
+        lo = np.ascontiguousarray(box_lo, np.float32)
+        hi = np.ascontiguousarray(box_hi, np.float32)
+    st = lib().relearn_morton_order_noalloc(n, px, py, pz, _np_ptr(lo), _np_ptr(hi), pc, pp,
+                                            _stream(stream))
+    _raise(None, st, "relearn_morton_order_noalloc")
 
 
 def relearn_last_error(ctx):
