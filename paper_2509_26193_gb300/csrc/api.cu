@@ -75,8 +75,8 @@ void free_all(relearn_ctx *c)
         (void **)&c->d_pos,      (void **)&c->d_mask,       (void **)&c->d_base,
         (void **)&c->d_nodes,    (void **)&c->d_parent,     (void **)&c->d_nchild,
         (void **)&c->d_leaf,     (void **)&c->d_acc,        (void **)&c->d_arrive,
-        (void **)&c->d_cnt,      (void **)&c->d_qoff_s,     (void **)&c->d_qoff_o,
-        (void **)&c->d_qsrc,     (void **)&c->d_req_src,    (void **)&c->d_req_elem,
+        (void **)&c->d_cnt,      (void **)&c->d_act_off,    (void **)&c->d_qoff_o,
+        (void **)&c->d_act_src,  (void **)&c->d_req_src,    (void **)&c->d_req_elem,
         (void **)&c->d_req_tgt,  (void **)&c->d_req_acc,    (void **)&c->d_req_prio,
         (void **)&c->d_bucket,   (void **)&c->d_tcnt,       (void **)&c->d_toff,
         (void **)&c->d_tfill,    (void **)&c->d_newpos,     (void **)&c->d_diag_lns,
@@ -186,9 +186,9 @@ relearn_status relearn_create(relearn_ctx **out, int device, int64_t max_neurons
     A(d_acc, 4 * M);
     A(d_arrive, M);
     A(d_cnt, N + 1);
-    A(d_qoff_s, N + 1);
+    A(d_act_off, N + 1);
     A(d_qoff_o, N + 1);
-    A(d_qsrc, QC);
+    A(d_act_src, N);
     A(d_req_src, QC);
     A(d_req_elem, QC);
     A(d_req_tgt, QC);
@@ -319,7 +319,7 @@ relearn_status relearn_update_connectivity(relearn_ctx *c, const relearn_params 
     if (timed) CK(cudaEventRecord(c->ev[2], st), "event");
     const bool ring = (p->flags & RELEARN_FLAG_TIMING) && c->nkev < 64;
     if (ring) CK(cudaEventRecord(c->kev[c->nkev][0], st), "event");
-    CK(search_run(c, *p, st), "search");
+    CK(search_run(c, *p, vac_ax, st), "search");
     if (ring) CK(cudaEventRecord(c->kev[c->nkev++][1], st), "event");
     if (timed) CK(cudaEventRecord(c->ev[3], st), "event");
     CK(accept_requests(c, *p, vac_de, st), "accept");
@@ -479,13 +479,19 @@ relearn_status relearn_get_tree(relearn_ctx *c, int64_t capacity, int64_t *num_n
     if (depth || first || size || is_leaf || neuron || count || cx || cy || cz) {
         if (capacity < m) return fail(c, RELEARN_ERR_INVALID_ARG, "get_tree: capacity");
         std::vector<Node> h(m);
+        std::vector<int32_t> par(m);
         CK(cudaMemcpy(h.data(), c->d_nodes, m * sizeof(Node), cudaMemcpyDeviceToHost), "copy");
+        CK(cudaMemcpy(par.data(), c->d_parent, m * sizeof(int32_t), cudaMemcpyDeviceToHost),
+           "copy");
         for (int64_t v = 0; v < m; ++v) {
             const Node &nd = h[v];
-            const bool leaf = (nd.t.meta & kLeafBit) != 0;
+            const bool leaf = node_is_leaf(nd.t.shift);
             const int32_t f = nd.t.neuron;
             const int32_t fe = nd.t.escape < m ? h[nd.t.escape].t.neuron : (int32_t)n;
-            if (depth) depth[v] = nd.t.meta & 15;
+            // a leaf sits one level below its parent (depth 11 inside a bucket)
+            const int dep = leaf ? (par[v] >= 0 ? depth_of(h[par[v]].t.shift) + 1 : 0)
+                                 : depth_of(nd.t.shift);
+            if (depth) depth[v] = dep;
             if (first) first[v] = f;
             if (size) size[v] = leaf ? 1 : fe - f;
             if (is_leaf) is_leaf[v] = leaf;

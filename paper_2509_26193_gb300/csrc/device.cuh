@@ -59,17 +59,26 @@ struct __align__(16) NodeGeo {
     float cnt;        // vacant dendritic elements, as float
 };
 struct __align__(16) NodeTopo {
-    int32_t escape; // pre-order index just past this node's subtree
-    int32_t meta;   // bits 0..3 depth (0..11), bit 4 leaf
-    int32_t neuron; // leaves: Morton position of the neuron; inner: first position
-    int32_t icount; // vacant dendritic elements, exact
+    int32_t escape;  // pre-order index just past this node's subtree
+    uint32_t shift;  // inner node of depth d: d << 24; leaf: kLeafShift (see below)
+    int32_t neuron;  // leaves: Morton position of the neuron; inner: first position
+    int32_t icount;  // vacant dendritic elements, exact
 };
 struct __align__(32) Node {
     NodeGeo g;
     NodeTopo t;
 };
 
-constexpr int kLeafBit = 16;
 constexpr int kMaxDepth = 10;
+
+// The acceptance test of a node at depth d, d^2 > thr0 / 4^d, is evaluated as
+// d^2 * 4^d > thr0 by adding d << 24 to the bits of d^2 (2d to its exponent;
+// exact, as is the division of thr0 by 4^d), and comparing the result as an
+// unsigned integer with the bits of thr0 (positive floats order like their
+// bits). A leaf gets a shift so large that the sum always exceeds any finite
+// thr0: single neurons are always accepted.
+constexpr uint32_t kLeafShift = 0x7F800000u;
+__host__ __device__ __forceinline__ bool node_is_leaf(uint32_t shift) { return shift == kLeafShift; }
+__host__ __device__ __forceinline__ int depth_of(uint32_t shift) { return (int)(shift >> 24); }
 
 } // namespace rl

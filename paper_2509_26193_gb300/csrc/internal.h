@@ -31,9 +31,9 @@ struct Geom {
 
 // Per-update search constants computed on the device from Geom and params.
 struct SearchConst {
-    float thr[12]; // node accepted iff d^2 > thr[depth] (= (len_depth / theta)^2)
+    uint32_t thr0; // bits of (root cell length / theta)^2 (FLT_MAX for theta = 0)
     float k2;      // log2(e) / sigma^2
-    float pad[3];
+    float pad[2];
 };
 
 } // namespace rl
@@ -69,9 +69,9 @@ struct relearn_ctx {
 
     // ---- queries and requests (per update)
     int32_t *d_cnt = nullptr;       // [n + 1] scratch counts
-    int32_t *d_qoff_s = nullptr;    // [n + 1] query offsets, Morton order
+    int32_t *d_act_off = nullptr;   // [n + 1] rank of each Morton position among active sources
     int32_t *d_qoff_o = nullptr;    // [n + 1] request offsets, id order
-    int32_t *d_qsrc = nullptr;      // [max_searches] Morton position per query
+    int32_t *d_act_src = nullptr;   // [n] Morton positions of neurons with vacant axons
     int32_t *d_req_src = nullptr;   // [max_searches] canonical order
     int32_t *d_req_elem = nullptr;  // [max_searches]
     int32_t *d_req_tgt = nullptr;   // [max_searches]
@@ -110,8 +110,8 @@ struct relearn_ctx {
 
 // slots of d_i64 / d_i32
 enum { I64_Q = 0, I64_FAILED, I64_DECLINED, I64_FORMED, I64_NSYN, I64_BROKEN, I64_SCAN_TOTAL,
-       I64_NODES, I64_Q_TOTAL, I64_EVALS_TOTAL };
-enum { I32_N = 0, I32_Q, I32_NSYN, I32_NEW, I32_NODES, I32_WORK };
+       I64_NODES, I64_Q_TOTAL, I64_EVALS_TOTAL, I64_ACTIVE };
+enum { I32_N = 0, I32_Q, I32_NSYN, I32_NEW, I32_NODES, I32_WORK, I32_ACTIVE };
 
 namespace rl {
 
@@ -147,7 +147,8 @@ cudaError_t octree_reduce(relearn_ctx *c, const int32_t *vac_de, cudaStream_t st
 // search.cu -----------------------------------------------------------------
 cudaError_t search_prepare(relearn_ctx *c, const relearn_params &p, const int32_t *vac_ax,
                            cudaStream_t st);
-cudaError_t search_run(relearn_ctx *c, const relearn_params &p, cudaStream_t st);
+cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *vac_ax,
+                       cudaStream_t st);
 
 // synapses.cu ---------------------------------------------------------------
 cudaError_t accept_requests(relearn_ctx *c, const relearn_params &p, const int32_t *vac_de,

@@ -252,7 +252,7 @@ __global__ void topo_emit_kernel(const uint32_t *__restrict__ codes, int64_t n,
             }
             Node nd;
             nd.g = NodeGeo{0.f, 0.f, 0.f, 0.f};
-            nd.t = NodeTopo{base[R + 1], d, (int32_t)i, 0};
+            nd.t = NodeTopo{base[R + 1], (uint32_t)d << 24, (int32_t)i, 0};
             nodes[v] = nd;
             parent[v] = par;
             if (par >= 0) atomicAdd(&nchild[par], 1);
@@ -261,18 +261,15 @@ __global__ void topo_emit_kernel(const uint32_t *__restrict__ codes, int64_t n,
         // the leaf of position i
         int32_t v = b + rank;
         int32_t par;
-        int ldepth;
         if (m) {
-            par = v - 1;
-            ldepth = 32 - __clz(m); // deepest node at i, plus one
+            par = v - 1; // the deepest node starting at i
         } else {
             int pd;
             par = parent_across(codes, mask, base, i, &pd);
-            ldepth = pd + 1;
         }
         Node nd;
         nd.g = NodeGeo{0.f, 0.f, 0.f, 0.f};
-        nd.t = NodeTopo{v + 1, ldepth | kLeafBit, (int32_t)i, 0};
+        nd.t = NodeTopo{v + 1, kLeafShift, (int32_t)i, 0};
         nodes[v] = nd;
         parent[v] = par;
         atomicAdd(&nchild[par], 1);

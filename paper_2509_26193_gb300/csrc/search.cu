@@ -1,83 +1,100 @@
 // Barnes-Hut partner search (Sec. III-B "Division of work", second paragraph;
 // acceptance criterion and theta from Sec. II).
 //
-// One thread per search (neuron i, element e). Searches are scheduled in
-// Morton order of their source, 32 consecutive ones per warp, so the lanes of a
-// warp walk nearly the same nodes. The walk over a start node's subtree is
-// stackless: nodes are stored in pre-order, so "expand" is p + 1 and "accept"
-// or "skip" jumps to the node's escape index. Candidates are therefore met in
-// Morton (range-start) order, which is the order of the cumulative draw.
+// Work item = one source neuron with vacant axonal elements. All searches of a
+// neuron start at the root from the same position, so their root frontier and
+// its total attraction S are identical; only the Philox draw differs. The root
+// frontier is therefore evaluated once per neuron and each of the neuron's
+// searches then draws from it (results are exactly those of separate searches).
 //
-// Per draw, pass 1 sums the attractions a = count * 2^(-k2 d^2) (k2 = log2(e) /
-// sigma^2) of the accepted candidates; pass 2 repeats the identical arithmetic
-// (explicit round-to-nearest intrinsics, no contraction freedom) until the
-// running sum exceeds u * S, so the drawn candidate is exactly the one whose
-// cumulative interval holds u * S. If every term would underflow, pass 1 is
-// redone with the exponents shifted by the nearest candidate's d^2 (an exact
-// common factor).
+// Root pass (pass 1): the 32 lanes of a warp take 32 neurons that are adjacent
+// in Morton order and walk the UNION of their frontiers together. Nodes are in
+// pre-order with skip links, so the walk is stackless: the warp descends
+// (p + 1) if any lane rejects the node under the acceptance criterion, else
+// jumps to the node's escape index. A lane that accepted a node ignores the
+// node's subtree; every node is loaded once per warp (one broadcast load), and
+// each lane still meets exactly its own candidates in Morton order, which is the
+// order of the cumulative draw. Every kCkStride warp steps each lane stores a
+// checkpoint (its next own node, its running sum).
+//
+// Draw (pass 2): u * S is located between two checkpoints by binary search and
+// the lane walks its own candidates from there, repeating pass 1's arithmetic
+// bit for bit (explicit round-to-nearest intrinsics), until the running sum
+// exceeds u * S. An inner node that is drawn restarts the search from itself;
+// restart frontiers are small and are walked per lane (sum, then find).
+//
+// Attraction a = count * 2^(-k2 d^2 + k2sh), k2 = log2(e) / sigma^2. k2sh = 0
+// unless every term would underflow, in which case the pass is redone with the
+// exponents shifted by the nearest candidate's d^2 (an exact common factor).
 #include "internal.h"
 
 namespace rl {
 
 namespace {
 
+constexpr int kCkStride = 128; // warp steps between checkpoints
+constexpr int kMaxCk = 128;    // checkpoints kept per lane (later steps reuse the last one)
+constexpr float kTiny = 8.673617e-19f; // 2^-60
+
+// A node of depth d is accepted iff d^2 > thr0 / 4^d, thr0 = (root length / theta)^2
+// rounded to FP32 (see NodeTopo::shift). theta = 0 accepts no inner node.
 __global__ void search_const_kernel(const Geom *g, float sigma, float theta, SearchConst *sc)
 {
-    double ext = g->ext;
-    double th = (double)theta;
-    for (int d = 0; d < 12; ++d) {
-        double len = ext / (double)(1u << d);
-        sc->thr[d] = th > 0.0 ? (float)((len / th) * (len / th)) : __int_as_float(0x7f800000);
-    }
-    double s = (double)sigma;
+    const double ext = g->ext, th = (double)theta;
+    const float thr0 = th > 0.0 ? (float)((ext / th) * (ext / th)) : 3.4028234663852886e38f;
+    sc->thr0 = __float_as_uint(fminf(thr0, 3.4028234663852886e38f));
+    const double s = (double)sigma;
     sc->k2 = (float)(1.4426950408889634 / (s * s));
 }
 
+// active[s] = 1 if the neuron at Morton position s has vacant axonal elements;
+// cnt_id[i] = its number of searches (canonical request order is by id).
 __global__ void query_counts_kernel(const int32_t *__restrict__ vac_ax,
                                     const int32_t *__restrict__ perm, int64_t n,
-                                    int32_t *__restrict__ cnt_sorted, int32_t *__restrict__ cnt_id)
+                                    int32_t *__restrict__ active, int32_t *__restrict__ cnt_id)
 {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= n;
          s += (int64_t)gridDim.x * blockDim.x) {
         if (s == n) {
-            cnt_sorted[n] = 0;
+            active[n] = 0;
             cnt_id[n] = 0;
             continue;
         }
-        int32_t a = vac_ax[perm[s]];
-        cnt_sorted[s] = a > 0 ? a : 0;
+        active[s] = vac_ax[perm[s]] > 0 ? 1 : 0;
         int32_t b = vac_ax[s];
         cnt_id[s] = b > 0 ? b : 0;
     }
 }
 
-// Q = total; beyond capacity the update is void (status CAPACITY, Q = 0).
-__global__ void query_check_kernel(const int64_t *d_total, int64_t max_searches, int32_t *d_Q,
+// Q = total searches; beyond capacity the update is void (status CAPACITY).
+__global__ void query_check_kernel(const int64_t *d_total, const int64_t *d_active,
+                                   int64_t max_searches, int32_t *d_Q, int32_t *d_A,
                                    int64_t *d_Qout, int64_t *d_Qsum, int32_t *status)
 {
     int64_t q = *d_total;
+    int64_t a = *d_active;
     *d_Qout = q;
     if (q > max_searches) {
         set_status(status, RELEARN_ERR_CAPACITY);
         q = 0;
+        a = 0;
     }
     *d_Q = (int32_t)q;
+    *d_A = (int32_t)a;
     *d_Qsum += q;
 }
 
-__global__ void query_fill_kernel(const int32_t *__restrict__ vac_ax,
-                                  const int32_t *__restrict__ perm, int64_t n,
-                                  const int32_t *__restrict__ qoff_s,
+__global__ void query_fill_kernel(const int32_t *__restrict__ vac_ax, int64_t n,
+                                  const int32_t *__restrict__ active,
+                                  const int32_t *__restrict__ act_off,
                                   const int32_t *__restrict__ qoff_o, const int32_t *d_Q,
-                                  int32_t *__restrict__ qsrc, int32_t *__restrict__ req_src,
+                                  int32_t *__restrict__ act_src, int32_t *__restrict__ req_src,
                                   int32_t *__restrict__ req_elem, int32_t *__restrict__ req_tgt)
 {
     if (*d_Q == 0) return;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (int64_t)gridDim.x * blockDim.x) {
-        int32_t a = vac_ax[perm[s]];
-        int32_t b0 = qoff_s[s];
-        for (int32_t e = 0; e < a; ++e) qsrc[b0 + e] = (int32_t)s;
+        if (active[s]) act_src[act_off[s]] = (int32_t)s;
         int32_t c = vac_ax[s];
         int32_t b1 = qoff_o[s];
         for (int32_t e = 0; e < c; ++e) {
@@ -92,10 +109,11 @@ struct SearchArgs {
     const Node *__restrict__ nodes;
     const float4 *__restrict__ pos;
     const int32_t *__restrict__ perm;
-    const int32_t *__restrict__ qsrc;
-    const int32_t *__restrict__ qoff_s;
+    const int32_t *__restrict__ act_src;
+    const int32_t *__restrict__ leaf_of;
+    const int32_t *__restrict__ vac_ax;
     const int32_t *__restrict__ qoff_o;
-    const int32_t *d_Q;
+    const int32_t *d_A;
     const SearchConst *sc;
     int32_t *work;
     int32_t *req_tgt;
@@ -115,30 +133,41 @@ struct WalkOut {
     int32_t evals;
 };
 
-// Walk the subtree of `start`, visiting exactly the candidates of its frontier.
-// FIND = false: total attraction and nearest d^2. FIND = true: first candidate
-// whose running sum exceeds `target` (else the last one with weight).
+// Attraction of one candidate; shared by every pass so the sums agree bit for bit.
+__device__ __forceinline__ float attraction(float cnt, float d2, float k2, float k2sh)
+{
+    return __fmul_rn(cnt, ex2_approx(__fmaf_rn(-k2, d2, k2sh)));
+}
+
+__device__ __forceinline__ float dist2(float3 x, float4 g)
+{
+    const float dx = __fsub_rn(x.x, g.x), dy = __fsub_rn(x.y, g.y), dz = __fsub_rn(x.z, g.z);
+    return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+}
+
+// One lane's own walk over [p0, end) starting from running sum cum0: visits
+// exactly its candidates (expand = p + 1, accept or empty = escape).
+// FIND = false: total attraction, nearest d^2, evaluations.
+// FIND = true: first candidate whose running sum exceeds `target` (else the
+// last one with weight, or -1).
 template <bool FIND>
-__device__ __forceinline__ WalkOut walk(const Node *__restrict__ nodes, int32_t start, float3 x,
-                                        int32_t self, const float *thr, float k2, float k2sh,
-                                        float target)
+__device__ __forceinline__ WalkOut walk(const Node *__restrict__ nodes, int32_t p0, int32_t end,
+                                        float cum0, float3 x, int32_t self_node, uint32_t thr0,
+                                        float k2, float k2sh, float target)
 {
     WalkOut o{0.0f, __int_as_float(0x7f800000), -1, 0};
-    int32_t p = start + 1;
-    const int32_t end = __ldg(&nodes[start].t.escape);
-    float cum = 0.0f;
+    int32_t p = p0;
+    float cum = cum0;
     while (p < end) {
         const float4 g = __ldg(reinterpret_cast<const float4 *>(&nodes[p].g));
-        const int4 t = __ldg(reinterpret_cast<const int4 *>(&nodes[p].t));
-        const float dx = __fsub_rn(x.x, g.x), dy = __fsub_rn(x.y, g.y), dz = __fsub_rn(x.z, g.z);
-        const float d2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+        const int2 t = __ldg(reinterpret_cast<const int2 *>(&nodes[p].t));
+        const float d2 = dist2(x, g);
         const bool has = g.w > 0.0f;
-        const bool leaf = (t.y & kLeafBit) != 0;
-        const bool acc = has && (leaf || d2 > thr[t.y & 15]);
-        const bool take = acc && !(leaf && t.z == self);
+        const bool acc = has && (__float_as_uint(d2) + (uint32_t)t.y > thr0);
+        const bool take = acc && p != self_node;
         if (!FIND) o.evals += has ? 1 : 0;
         if (take) {
-            const float a = __fmul_rn(g.w, ex2_approx(__fmaf_rn(-k2, d2, k2sh)));
+            const float a = attraction(g.w, d2, k2, k2sh);
             cum = __fadd_rn(cum, a);
             if (FIND) {
                 if (a > 0.0f) o.pick = p;
@@ -148,7 +177,7 @@ __device__ __forceinline__ WalkOut walk(const Node *__restrict__ nodes, int32_t 
             }
         }
         // t.x > p holds for every well-formed node; max() keeps the walk finite regardless
-        p = (has && !leaf && !acc) ? p + 1 : max(t.x, p + 1);
+        p = (has && !acc) ? p + 1 : max(t.x, p + 1);
     }
     o.sum = cum;
     return o;
@@ -156,69 +185,140 @@ __device__ __forceinline__ WalkOut walk(const Node *__restrict__ nodes, int32_t 
 
 __global__ void __launch_bounds__(256) bh_search_kernel(SearchArgs a)
 {
-    __shared__ float s_thr[12];
-    __shared__ float s_k2;
-    if (threadIdx.x < 12) s_thr[threadIdx.x] = a.sc->thr[threadIdx.x];
-    if (threadIdx.x == 0) s_k2 = a.sc->k2;
-    __syncthreads();
-    const float k2 = s_k2;
-    const int32_t Q = *a.d_Q;
+    const uint32_t thr0 = __ldg(&a.sc->thr0);
+    const float k2 = __ldg(&a.sc->k2);
+    const int32_t A = *a.d_A;
+    const int32_t root_end = __ldg(&a.nodes[0].t.escape);
     const int lane = threadIdx.x & 31;
-    int64_t warp_evals = 0; // node evaluations of this lane's searches
+    int64_t my_evals = 0;
+    int32_t ckp[kMaxCk];
+    float ckc[kMaxCk];
     for (;;) {
-        int32_t qb = 0;
-        if (lane == 0) qb = atomicAdd(a.work, 32);
-        qb = __shfl_sync(0xffffffffu, qb, 0);
-        if (qb >= Q) break;
-        const int32_t q = qb + lane;
-        if (q >= Q) continue;
-        const int32_t s = a.qsrc[q];
-        const int32_t e = q - a.qoff_s[s];
-        const int32_t i = a.perm[s];
-        const float4 xp = a.pos[s];
+        int32_t nb = 0;
+        if (lane == 0) nb = atomicAdd(a.work, 32);
+        nb = __shfl_sync(0xffffffffu, nb, 0);
+        if (nb >= A) break;
+        const int32_t slot = nb + lane;
+        const bool live = slot < A;
+        const int32_t s = live ? a.act_src[slot] : -1;
+        const float4 xp = live ? a.pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float3 x = make_float3(xp.x, xp.y, xp.z);
-        int32_t start = 0, sdepth = 0, result = -1, evals = 0, draws = 0;
-        double lns0 = -__longlong_as_double(0x7ff0000000000000LL);
-        for (int hop = 0; hop < 24; ++hop) {
-            float k2sh = 0.0f;
-            WalkOut w1 = walk<false>(a.nodes, start, x, s, s_thr, k2, 0.0f, 0.0f);
-            evals += w1.evals;
-            if (w1.sum < 8.673617e-19f && w1.dmin2 < __int_as_float(0x7f800000)) {
-                // 2^-60: redo with an exact common factor so nothing underflows
-                k2sh = __fmul_rn(k2, w1.dmin2);
-                w1 = walk<false>(a.nodes, start, x, s, s_thr, k2, k2sh, 0.0f);
+        const int32_t self_node = live ? a.leaf_of[s] : -1;
+
+        // ---- pass 1: the union of the 32 root frontiers, one broadcast load per node
+        float k2sh = 0.0f, S = 0.0f;
+        int32_t own = 0, nck = 0;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            int32_t p = 1, skip = live ? 0 : 0x7fffffff;
+            float cum = 0.0f;
+            own = 0;
+            nck = 0;
+            while (p < root_end) {
+                if (nck < kMaxCk) {
+                    ckp[nck] = max(p, skip);
+                    ckc[nck] = cum;
+                    ++nck;
+                }
+#pragma unroll 1
+                for (int k = 0; k < kCkStride && p < root_end; ++k) {
+                    const float4 g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[p].g));
+                    const int2 t = __ldg(reinterpret_cast<const int2 *>(&a.nodes[p].t));
+                    const float d2 = dist2(x, g);
+                    const bool on = p >= skip && g.w > 0.0f;
+                    const bool pass = __float_as_uint(d2) + (uint32_t)t.y > thr0;
+                    own += on ? 1 : 0;
+                    if (on && pass) {
+                        skip = t.x;
+                        if (p != self_node) cum = __fadd_rn(cum, attraction(g.w, d2, k2, k2sh));
+                    }
+                    p = __any_sync(0xffffffffu, on && !pass) ? p + 1 : max(t.x, p + 1);
+                }
             }
-            if (!(w1.sum > 0.0f)) break;
-            if (hop == 0)
-                lns0 = log((double)w1.sum) - (double)k2sh * 0.6931471805599453;
-            const uint32_t u = philox_x((uint32_t)i, a.step, ((uint32_t)e << 8) | (uint32_t)sdepth,
-                                        0u, a.seed);
-            const float target = (float)((double)u * 2.3283064365386963e-10 * (double)w1.sum);
-            WalkOut w2 = walk<true>(a.nodes, start, x, s, s_thr, k2, k2sh, target);
-            ++draws;
-            const int32_t k = w2.pick;
-            const int4 tk = __ldg(reinterpret_cast<const int4 *>(&a.nodes[k].t));
-            if (tk.y & kLeafBit) {
-                result = a.perm[tk.z];
-                break;
+            S = cum;
+            // every term underflowed: redo with the exponents shifted by the nearest d^2
+            const bool redo = live && cum < kTiny;
+            if (!__any_sync(0xffffffffu, redo)) break;
+            if (redo) {
+                const WalkOut w = walk<false>(a.nodes, 1, root_end, 0.0f, x, self_node, thr0, k2,
+                                              k2sh, 0.0f);
+                if (w.dmin2 < __int_as_float(0x7f800000)) k2sh = __fmul_rn(k2, w.dmin2);
             }
-            start = k;
-            sdepth = tk.y & 15;
         }
-        const int32_t slot = a.qoff_o[i] + e;
-        warp_evals += evals;
-        a.req_tgt[slot] = result;
-        if (result < 0) atomicAdd(reinterpret_cast<unsigned long long *>(a.failed), 1ull);
-        if (a.diag_lns) {
-            a.diag_lns[slot] = lns0;
-            a.diag_evals[slot] = evals;
-            a.diag_restarts[slot] = draws > 0 ? draws - 1 : 0;
+        if (!live) continue;
+        my_evals += own;
+
+        // ---- draws: every search of this neuron
+        const int32_t i = a.perm[s];
+        const int32_t nq = max(a.vac_ax[i], 0);
+        const int32_t qbase = a.qoff_o[i];
+        const double lns0 =
+            S > 0.0f ? log((double)S) - (double)k2sh * 0.6931471805599453
+                     : -__longlong_as_double(0x7ff0000000000000LL);
+        for (int32_t e = 0; e < nq; ++e) {
+            int32_t result = -1, evals = own, draws = 0;
+            if (S > 0.0f) {
+                uint32_t u = philox_x((uint32_t)i, a.step, (uint32_t)e << 8, 0u, a.seed);
+                float target = (float)((double)u * 2.3283064365386963e-10 * (double)S);
+                int lo = 0, hi = nck - 1; // last checkpoint whose running sum <= target
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (ckc[mid] <= target)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                WalkOut w = walk<true>(a.nodes, ckp[lo], root_end, ckc[lo], x, self_node, thr0,
+                                       k2, k2sh, target);
+                if (w.pick < 0) // u * S rounded up to S past the last weighted candidate
+                    w = walk<true>(a.nodes, 1, root_end, 0.0f, x, self_node, thr0, k2, k2sh,
+                                   __int_as_float(0x7f800000));
+                int32_t k = w.pick;
+                draws = 1;
+                while (k >= 0 && draws < 24) {
+                    const int4 tk = __ldg(reinterpret_cast<const int4 *>(&a.nodes[k].t));
+                    if (node_is_leaf((uint32_t)tk.y)) {
+                        result = a.perm[tk.z];
+                        break;
+                    }
+                    // restart at the drawn inner node: its frontier is walked per lane
+                    const int32_t kend = tk.x;
+                    float sh = 0.0f;
+                    WalkOut w1 = walk<false>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2,
+                                             0.0f, 0.0f);
+                    evals += w1.evals;
+                    my_evals += w1.evals;
+                    if (w1.sum < kTiny && w1.dmin2 < __int_as_float(0x7f800000)) {
+                        sh = __fmul_rn(k2, w1.dmin2);
+                        w1 = walk<false>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2, sh,
+                                         0.0f);
+                    }
+                    if (!(w1.sum > 0.0f)) {
+                        k = -1;
+                        break;
+                    }
+                    u = philox_x((uint32_t)i, a.step,
+                                 ((uint32_t)e << 8) | (uint32_t)depth_of((uint32_t)tk.y), 0u,
+                                 a.seed);
+                    target = (float)((double)u * 2.3283064365386963e-10 * (double)w1.sum);
+                    k = walk<true>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2, sh, target)
+                            .pick;
+                    ++draws;
+                }
+            }
+            const int32_t out = qbase + e;
+            a.req_tgt[out] = result;
+            if (result < 0) atomicAdd(reinterpret_cast<unsigned long long *>(a.failed), 1ull);
+            if (a.diag_lns) {
+                a.diag_lns[out] = lns0;
+                a.diag_evals[out] = evals;
+                a.diag_restarts[out] = draws > 0 ? draws - 1 : 0;
+            }
         }
     }
-    for (int off = 16; off; off >>= 1) warp_evals += __shfl_xor_sync(0xffffffffu, warp_evals, off);
-    if (lane == 0 && warp_evals)
+    for (int off = 16; off; off >>= 1) my_evals += __shfl_xor_sync(0xffffffffu, my_evals, off);
+    if (lane == 0 && my_evals)
         atomicAdd(reinterpret_cast<unsigned long long *>(a.evals_total),
-                  (unsigned long long)warp_evals);
+                  (unsigned long long)my_evals);
 }
 
 inline unsigned grid_for(int64_t n, int threads, int num_sms)
@@ -239,26 +339,29 @@ cudaError_t search_prepare(relearn_ctx *c, const relearn_params &p, const int32_
     const int64_t n = c->n;
     search_const_kernel<<<1, 1, 0, st>>>(c->d_geom, p.sigma, p.theta, c->d_sc);
     note_launch();
-    int32_t *cnt_s = c->d_cnt, *cnt_o = c->d_tcnt; // scratch
+    int32_t *active = c->d_cnt, *cnt_o = c->d_tcnt; // scratch
     query_counts_kernel<<<grid_for(n + 1, 256, c->num_sms), 256, 0, st>>>(vac_ax, c->d_perm, n,
-                                                                          cnt_s, cnt_o);
+                                                                          active, cnt_o);
     note_launch();
-    if ((e = scan_exclusive(cnt_s, c->d_qoff_s, n + 1, nullptr, c->d_i64 + I64_SCAN_TOTAL,
+    if ((e = scan_exclusive(active, c->d_act_off, n + 1, nullptr, c->d_i64 + I64_ACTIVE, c->scan,
+                            st)))
+        return e;
+    if ((e = scan_exclusive(cnt_o, c->d_qoff_o, n + 1, nullptr, c->d_i64 + I64_SCAN_TOTAL,
                             c->scan, st)))
         return e;
-    if ((e = scan_exclusive(cnt_o, c->d_qoff_o, n + 1, nullptr, nullptr, c->scan, st))) return e;
-    query_check_kernel<<<1, 1, 0, st>>>(c->d_i64 + I64_SCAN_TOTAL, c->max_searches,
-                                        c->d_i32 + I32_Q, c->d_i64 + I64_Q,
-                                        c->d_i64 + I64_Q_TOTAL, c->d_status);
+    query_check_kernel<<<1, 1, 0, st>>>(c->d_i64 + I64_SCAN_TOTAL, c->d_i64 + I64_ACTIVE,
+                                        c->max_searches, c->d_i32 + I32_Q, c->d_i32 + I32_ACTIVE,
+                                        c->d_i64 + I64_Q, c->d_i64 + I64_Q_TOTAL, c->d_status);
     note_launch();
     query_fill_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(
-        vac_ax, c->d_perm, n, c->d_qoff_s, c->d_qoff_o, c->d_i32 + I32_Q, c->d_qsrc,
+        vac_ax, n, active, c->d_act_off, c->d_qoff_o, c->d_i32 + I32_Q, c->d_act_src,
         c->d_req_src, c->d_req_elem, c->d_req_tgt);
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t search_run(relearn_ctx *c, const relearn_params &p, cudaStream_t st)
+cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *vac_ax,
+                       cudaStream_t st)
 {
     cudaError_t e;
     if ((e = cudaMemsetAsync(c->d_i32 + I32_WORK, 0, sizeof(int32_t), st))) return e;
@@ -267,10 +370,11 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, cudaStream_t st)
     a.nodes = c->d_nodes;
     a.pos = c->d_pos;
     a.perm = c->d_perm;
-    a.qsrc = c->d_qsrc;
-    a.qoff_s = c->d_qoff_s;
+    a.act_src = c->d_act_src;
+    a.leaf_of = c->d_leaf;
+    a.vac_ax = vac_ax;
     a.qoff_o = c->d_qoff_o;
-    a.d_Q = c->d_i32 + I32_Q;
+    a.d_A = c->d_i32 + I32_ACTIVE;
     a.sc = c->d_sc;
     a.work = c->d_i32 + I32_WORK;
     a.req_tgt = c->d_req_tgt;
