@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--group", type=int, default=0,
+                    help="source neurons per octree walk in the search kernel (0 = default)")
     return ap.parse_args()
 
 
@@ -150,11 +152,12 @@ class ClockSampler:
 
 # ------------------------------------------------------------------- our arm
 class Runner:
-    def __init__(self, net, theta, device):
+    def __init__(self, net, theta, device, group=0):
         import torch
         from paper_2509_26193_gb300 import build, relearn as R, workloads
         build.build()
         self.torch, self.R, self.net, self.theta = torch, R, net, theta
+        self.group = group
         self.dev = device
         n = net.n
         d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
@@ -201,7 +204,8 @@ class Runner:
         R.relearn_build_octree(self.ctx, self.x, self.y, self.z)
         base = 1000 * self.step_index
         for u in range(UPDATES_PER_STEP):
-            p = R.params(self.net.sigma, self.theta, self.net.seed, base + u, R.FLAG_TIMING)
+            p = R.params(self.net.sigma, self.theta, self.net.seed, base + u, R.FLAG_TIMING,
+                         self.group)
             R.relearn_update_connectivity(self.ctx, p, self.vac_ax, self.vac_de, self.type)
             R.relearn_deliver_spikes(self.ctx, self.spiked[u], self.input)
         p = R.params(self.net.sigma, self.theta, self.net.seed, base + 999)
@@ -213,13 +217,13 @@ class Runner:
 
     def counters(self):
         s = self.R.relearn_get_last_stats(self.ctx)
-        return s["searches_total"], s["evals_total"]
+        return s["searches_total"], s["evals_total"], s["walk_steps_total"]
 
     def timed(self, steps, e2e):
         torch = self.torch
         st = torch.cuda.current_stream()
         total_ms = 0.0
-        q0, e0 = self.counters()
+        q0, e0, w0 = self.counters()
         self.R.relearn_collect_search_times(self.ctx)
         k_ms, k_n = 0.0, 0
         l0 = self.R.relearn_launch_count()
@@ -237,8 +241,9 @@ class Runner:
             k_ms += ms
             k_n += kn
         launches = self.R.relearn_launch_count() - l0
-        q1, e1 = self.counters()
-        return {"ms": total_ms, "searches": q1 - q0, "evals": e1 - e0, "kernel_ms": k_ms,
+        q1, e1, w1 = self.counters()
+        return {"ms": total_ms, "searches": q1 - q0, "evals": e1 - e0, "walk_steps": w1 - w0,
+                "kernel_ms": k_ms,
                 "kernel_launches": k_n, "launches": launches}
 
 
@@ -248,7 +253,7 @@ def first_update_profile(runner):
     runner.vac_ax.copy_(runner.vac_ax0)
     runner.vac_de.copy_(runner.vac_de0)
     R.relearn_build_octree(runner.ctx, runner.x, runner.y, runner.z)
-    p = R.params(runner.net.sigma, runner.theta, runner.net.seed, 0)
+    p = R.params(runner.net.sigma, runner.theta, runner.net.seed, 0, 0, runner.group)
     s = R.relearn_update_connectivity(runner.ctx, p, runner.vac_ax, runner.vac_de, runner.type,
                                       stats=True)
     p = R.params(runner.net.sigma, runner.theta, runner.net.seed, 999)
@@ -338,7 +343,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(net, args.theta)  # before any CUDA context-heavy work
-    run = Runner(net, args.theta, device)
+    run = Runner(net, args.theta, device, args.group)
     prof = first_update_profile(run)
     for _ in range(max(args.warmup, 3)):
         run.step()
@@ -395,7 +400,9 @@ def run_ours(args):
                                  "ms_search_kernel": prof["ms_search_kernel"],
                                  "ms_accept": prof["ms_accept"], "ms_apply": prof["ms_apply"],
                                  "searches_per_s": prof["searches"] / (prof["ms_total"] / 1e3)},
-                "evals_per_search": res["evals"] / max(res["searches"], 1)}),
+                "evals_per_search": res["evals"] / max(res["searches"], 1),
+                "search_group": args.group or "default",
+                "walk_steps_per_search": res["walk_steps"] / max(res["searches"], 1)}),
             "clocks": clk, "e2e": e2e, "gpu_launches": res["launches"],
             "roofline": roof, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)

@@ -53,14 +53,16 @@ typedef struct relearn_ctx relearn_ctx;
  *             (Sec. II; theta = 0 gives the exact O(n^2) draw).
  *   seed      key of every Philox4x32-10 draw.
  *   step      update index (< 2^32), part of every Philox counter.
- *   flags     RELEARN_FLAG_* bits. */
+ *   flags     RELEARN_FLAG_* bits.
+ *   search_group  tuning only (results do not depend on it): how many source neurons walk
+ *             the octree together in the search kernel, 8, 16 or 32; 0 = library default. */
 typedef struct {
     float sigma;
     float theta;
     uint64_t seed;
     uint64_t step;
     uint32_t flags;
-    uint32_t reserved;
+    uint32_t search_group;
 } relearn_params;
 
 /* Record per-search diagnostics (root-frontier ln S, node evaluations, restarts),
@@ -87,6 +89,8 @@ typedef struct {
     int64_t searches_total;     /* searches of every update since the context was created */
     int64_t evals_total;        /* node evaluations (count > 0) of those searches: the
                                    algorithmic work of the search, one per frontier candidate */
+    int64_t walk_steps_total;   /* node visits of the grouped root-frontier walks (one node load
+                                   per group of source neurons), for the same updates */
 } relearn_update_stats;
 
 /* Create a context on CUDA device `device` that can hold up to max_neurons

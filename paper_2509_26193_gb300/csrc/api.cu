@@ -73,8 +73,8 @@ void free_all(relearn_ctx *c)
         (void **)&c->d_geom,     (void **)&c->d_sc,         (void **)&c->d_codes,
         (void **)&c->d_codes_alt, (void **)&c->d_perm,      (void **)&c->d_perm_alt,
         (void **)&c->d_pos,      (void **)&c->d_mask,       (void **)&c->d_base,
-        (void **)&c->d_nodes,    (void **)&c->d_parent,     (void **)&c->d_nchild,
-        (void **)&c->d_leaf,     (void **)&c->d_acc,        (void **)&c->d_arrive,
+        (void **)&c->d_nodes,    (void **)&c->d_parent,     (void **)&c->d_nsize,
+        (void **)&c->d_leaf,     (void **)&c->d_acc,
         (void **)&c->d_cnt,      (void **)&c->d_act_off,    (void **)&c->d_qoff_o,
         (void **)&c->d_act_src,  (void **)&c->d_req_src,    (void **)&c->d_req_elem,
         (void **)&c->d_req_tgt,  (void **)&c->d_req_acc,    (void **)&c->d_req_prio,
@@ -110,7 +110,9 @@ void free_all(relearn_ctx *c)
 bool params_ok(const relearn_params *p)
 {
     return p && p->sigma > 0.0f && p->sigma < 3.0e38f && p->theta >= 0.0f &&
-           p->theta < 3.0e38f && p->step <= 0xffffffffull;
+           p->theta < 3.0e38f && p->step <= 0xffffffffull &&
+           (p->search_group == 0 || p->search_group == 8 || p->search_group == 16 ||
+            p->search_group == 32);
 }
 
 relearn_status read_status(relearn_ctx *c)
@@ -169,7 +171,7 @@ relearn_status relearn_create(relearn_ctx **out, int device, int64_t max_neurons
     if (e == cudaSuccess) e = alloc(&c->ptr, (cnt), owned)
     A(d_status, 1);
     A(d_i64, 16);
-    A(d_i32, 16);
+    A(d_i32, 32);
     A(d_geom, 1);
     A(d_sc, 1);
     A(d_codes, N);
@@ -181,10 +183,9 @@ relearn_status relearn_create(relearn_ctx **out, int device, int64_t max_neurons
     A(d_base, N + 1);
     A(d_nodes, M);
     A(d_parent, M);
-    A(d_nchild, M);
+    A(d_nsize, M);
     A(d_leaf, N);
     A(d_acc, 4 * M);
-    A(d_arrive, M);
     A(d_cnt, N + 1);
     A(d_act_off, N + 1);
     A(d_qoff_o, N + 1);
@@ -241,7 +242,7 @@ relearn_status relearn_create(relearn_ctx **out, int device, int64_t max_neurons
     }
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->d_i64, 0, 16 * sizeof(int64_t));
-    if (e == cudaSuccess) e = cudaMemset(c->d_i32, 0, 16 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->d_i32, 0, 32 * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         relearn_status s = (e == cudaErrorMemoryAllocation) ? RELEARN_ERR_OOM : RELEARN_ERR_CUDA;
@@ -375,6 +376,7 @@ relearn_status relearn_get_synapses(relearn_ctx *c, int64_t capacity, int64_t *c
 {
     if (!c || !count) return RELEARN_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
+    if (c->built && !c->canonical) CK(canonicalise_store(c, c->last_stream), "canonicalise");
     relearn_status s = sync(c);
     int32_t m = 0;
     CK(cudaMemcpy(&m, c->d_i32 + I32_NSYN, sizeof(int32_t), cudaMemcpyDeviceToHost), "copy");
@@ -552,6 +554,7 @@ relearn_status relearn_get_last_stats(relearn_ctx *c, relearn_update_stats *stat
     stats->synapses = h[I64_NSYN];
     stats->searches_total = h[I64_Q_TOTAL];
     stats->evals_total = h[I64_EVALS_TOTAL];
+    stats->walk_steps_total = h[I64_STEPS_TOTAL];
     if (c->timed) {
         cudaEventElapsedTime(&stats->ms_reduce, c->ev[0], c->ev[1]);
         cudaEventElapsedTime(&stats->ms_search, c->ev[1], c->ev[3]);

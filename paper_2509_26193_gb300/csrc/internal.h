@@ -62,10 +62,10 @@ struct relearn_ctx {
     uint32_t *d_mask = nullptr;                          // [n] depths of nodes starting here
     int32_t *d_base = nullptr;                           // [n + 1] pre-order index of position
     rl::Node *d_nodes = nullptr;                         // [max_nodes]
-    int32_t *d_parent = nullptr, *d_nchild = nullptr;    // [max_nodes]
+    int32_t *d_parent = nullptr;                         // [max_nodes] (get_tree)
+    int32_t *d_nsize = nullptr;                          // [max_nodes] neurons in the node's cell
     int32_t *d_leaf = nullptr;                           // [n] leaf node of each position
-    double *d_acc = nullptr;                             // [4 * max_nodes] FP64 sums (reduce)
-    int32_t *d_arrive = nullptr;                         // [max_nodes]
+    double *d_acc = nullptr;  // [4 * max_nodes] FP64 prefix sums and block sums (reduce)
 
     // ---- queries and requests (per update)
     int32_t *d_cnt = nullptr;       // [n + 1] scratch counts
@@ -106,11 +106,12 @@ struct relearn_ctx {
     int nkev = 0;
     bool diag_valid = false;
     bool stats_valid = false;
+    bool canonical = true; // store sorted by (src, tgt) with stable views (else rows only)
 };
 
 // slots of d_i64 / d_i32
 enum { I64_Q = 0, I64_FAILED, I64_DECLINED, I64_FORMED, I64_NSYN, I64_BROKEN, I64_SCAN_TOTAL,
-       I64_NODES, I64_Q_TOTAL, I64_EVALS_TOTAL, I64_ACTIVE };
+       I64_NODES, I64_Q_TOTAL, I64_EVALS_TOTAL, I64_ACTIVE, I64_STEPS_TOTAL };
 enum { I32_N = 0, I32_Q, I32_NSYN, I32_NEW, I32_NODES, I32_WORK, I32_ACTIVE };
 
 namespace rl {
@@ -156,6 +157,7 @@ cudaError_t accept_requests(relearn_ctx *c, const relearn_params &p, const int32
 cudaError_t apply_requests(relearn_ctx *c, int32_t *vac_ax, int32_t *vac_de, const uint8_t *type,
                            cudaStream_t st);
 cudaError_t rebuild_views(relearn_ctx *c, cudaStream_t st);
+cudaError_t rebuild_in_rows(relearn_ctx *c, cudaStream_t st);
 cudaError_t delete_synapses(relearn_ctx *c, const relearn_params &p, const int32_t *retract_ax,
                             const int32_t *retract_de, int32_t *vac_ax, int32_t *vac_de,
                             cudaStream_t st);

@@ -35,6 +35,7 @@ namespace {
 constexpr int kCkStride = 128; // warp steps between checkpoints
 constexpr int kMaxCk = 128;    // checkpoints kept per lane (later steps reuse the last one)
 constexpr float kTiny = 8.673617e-19f; // 2^-60
+constexpr uint32_t kDefaultGroup = 16; // lanes per union walk unless params.search_group says
 
 // A node of depth d is accepted iff d^2 > thr0 / 4^d, thr0 = (root length / theta)^2
 // rounded to FP32 (see NodeTopo::shift). theta = 0 accepts no inner node.
@@ -119,6 +120,7 @@ struct SearchArgs {
     int32_t *req_tgt;
     int64_t *failed;
     int64_t *evals_total;
+    int64_t *steps_total;
     double *diag_lns;
     int32_t *diag_evals;
     int32_t *diag_restarts;
@@ -183,6 +185,9 @@ __device__ __forceinline__ WalkOut walk(const Node *__restrict__ nodes, int32_t 
     return o;
 }
 
+// G = lanes per union walk (8, 16 or 32). A warp runs 32 / G independent walks,
+// so 32 / G node loads are in flight per step, and each union covers fewer sources.
+template <int G>
 __global__ void __launch_bounds__(256) bh_search_kernel(SearchArgs a)
 {
     const uint32_t thr0 = __ldg(&a.sc->thr0);
@@ -190,7 +195,9 @@ __global__ void __launch_bounds__(256) bh_search_kernel(SearchArgs a)
     const int32_t A = *a.d_A;
     const int32_t root_end = __ldg(&a.nodes[0].t.escape);
     const int lane = threadIdx.x & 31;
-    int64_t my_evals = 0;
+    const uint32_t gmask =
+        G == 32 ? 0xffffffffu : (((1u << (G & 31)) - 1u) << (lane & ~(G - 1)));
+    int64_t my_evals = 0, my_steps = 0;
     int32_t ckp[kMaxCk];
     float ckc[kMaxCk];
     for (;;) {
@@ -205,35 +212,67 @@ __global__ void __launch_bounds__(256) bh_search_kernel(SearchArgs a)
         const float3 x = make_float3(xp.x, xp.y, xp.z);
         const int32_t self_node = live ? a.leaf_of[s] : -1;
 
-        // ---- pass 1: the union of the 32 root frontiers, one broadcast load per node
+        // ---- pass 1: union of the G root frontiers of this lane's group
         float k2sh = 0.0f, S = 0.0f;
         int32_t own = 0, nck = 0;
         for (int attempt = 0; attempt < 2; ++attempt) {
-            int32_t p = 1, skip = live ? 0 : 0x7fffffff;
+            int32_t p = 1, skip = live ? 0 : 0x7fffffff, steps = 0;
             float cum = 0.0f;
             own = 0;
             nck = 0;
-            while (p < root_end) {
-                if (nck < kMaxCk) {
-                    ckp[nck] = max(p, skip);
-                    ckc[nck] = cum;
-                    ++nck;
-                }
+            if constexpr (G == 32) {
+                // one walk per warp: every lane steps together, no group masks
+                while (p < root_end) {
+                    if (nck < kMaxCk) {
+                        ckp[nck] = max(p, skip);
+                        ckc[nck] = cum;
+                        ++nck;
+                    }
 #pragma unroll 1
-                for (int k = 0; k < kCkStride && p < root_end; ++k) {
-                    const float4 g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[p].g));
-                    const int2 t = __ldg(reinterpret_cast<const int2 *>(&a.nodes[p].t));
+                    for (int k = 0; k < kCkStride && p < root_end; ++k) {
+                        const float4 g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[p].g));
+                        const int2 t = __ldg(reinterpret_cast<const int2 *>(&a.nodes[p].t));
+                        const float d2 = dist2(x, g);
+                        const bool on = p >= skip && g.w > 0.0f;
+                        const bool pass = __float_as_uint(d2) + (uint32_t)t.y > thr0;
+                        own += on ? 1 : 0;
+                        if (on && pass) {
+                            skip = t.x;
+                            if (p != self_node)
+                                cum = __fadd_rn(cum, attraction(g.w, d2, k2, k2sh));
+                        }
+                        p = __any_sync(0xffffffffu, on && !pass) ? p + 1 : max(t.x, p + 1);
+                        ++steps;
+                    }
+                }
+            } else {
+                while (__any_sync(0xffffffffu, p < root_end)) {
+                    const bool run = p < root_end; // uniform within the group
+                    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+                    int2 t = make_int2(p + 1, 0);
+                    if (run) {
+                        if ((steps & (kCkStride - 1)) == 0 && nck < kMaxCk) {
+                            ckp[nck] = max(p, skip);
+                            ckc[nck] = cum;
+                            ++nck;
+                        }
+                        ++steps;
+                        g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[p].g));
+                        t = __ldg(reinterpret_cast<const int2 *>(&a.nodes[p].t));
+                    }
                     const float d2 = dist2(x, g);
-                    const bool on = p >= skip && g.w > 0.0f;
+                    const bool on = run && p >= skip && g.w > 0.0f;
                     const bool pass = __float_as_uint(d2) + (uint32_t)t.y > thr0;
                     own += on ? 1 : 0;
                     if (on && pass) {
                         skip = t.x;
                         if (p != self_node) cum = __fadd_rn(cum, attraction(g.w, d2, k2, k2sh));
                     }
-                    p = __any_sync(0xffffffffu, on && !pass) ? p + 1 : max(t.x, p + 1);
+                    const uint32_t down = __ballot_sync(0xffffffffu, on && !pass) & gmask;
+                    if (run) p = down ? p + 1 : max(t.x, p + 1);
                 }
             }
+            my_steps += steps;
             S = cum;
             // every term underflowed: redo with the exponents shifted by the nearest d^2
             const bool redo = live && cum < kTiny;
@@ -315,10 +354,16 @@ __global__ void __launch_bounds__(256) bh_search_kernel(SearchArgs a)
             }
         }
     }
-    for (int off = 16; off; off >>= 1) my_evals += __shfl_xor_sync(0xffffffffu, my_evals, off);
+    for (int off = 16; off; off >>= 1) {
+        my_evals += __shfl_xor_sync(0xffffffffu, my_evals, off);
+        my_steps += __shfl_xor_sync(0xffffffffu, my_steps, off);
+    }
     if (lane == 0 && my_evals)
         atomicAdd(reinterpret_cast<unsigned long long *>(a.evals_total),
                   (unsigned long long)my_evals);
+    if (lane == 0 && my_steps) // every lane of a group counted the group's steps
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.steps_total),
+                  (unsigned long long)(my_steps / G));
 }
 
 inline unsigned grid_for(int64_t n, int threads, int num_sms)
@@ -380,17 +425,21 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     a.req_tgt = c->d_req_tgt;
     a.failed = c->d_i64 + I64_FAILED;
     a.evals_total = c->d_i64 + I64_EVALS_TOTAL;
+    a.steps_total = c->d_i64 + I64_STEPS_TOTAL;
     const bool diag = (p.flags & RELEARN_FLAG_DIAG) != 0;
     a.diag_lns = diag ? c->d_diag_lns : nullptr;
     a.diag_evals = diag ? c->d_diag_evals : nullptr;
     a.diag_restarts = diag ? c->d_diag_restarts : nullptr;
     a.seed = p.seed;
     a.step = (uint32_t)p.step;
+    const uint32_t group = p.search_group ? p.search_group : kDefaultGroup;
+    void (*kern)(SearchArgs) = group == 8    ? bh_search_kernel<8>
+                               : group == 16 ? bh_search_kernel<16>
+                                             : bh_search_kernel<32>;
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bh_search_kernel, 256, 0)))
-        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0))) return e;
     if (per_sm < 1) per_sm = 1;
-    bh_search_kernel<<<c->num_sms * per_sm, 256, 0, st>>>(a);
+    kern<<<c->num_sms * per_sm, 256, 0, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }

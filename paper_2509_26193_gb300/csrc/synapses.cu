@@ -229,6 +229,31 @@ __global__ void in_view_kernel(const int32_t *d_nsyn, const int32_t *__restrict_
     }
 }
 
+// In-CSR by counting sort (rows by target; order inside a row is arbitrary):
+// enough for spike delivery, whose per-row sums are integers.
+__global__ void in_degree_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ tgt,
+                                 int32_t *__restrict__ in_cnt)
+{
+    const int64_t m = *d_nsyn;
+    GRID_STRIDE(k, m) atomicAdd(&in_cnt[tgt[k]], 1);
+}
+
+__global__ void in_scatter_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ src,
+                                  const int32_t *__restrict__ tgt,
+                                  const int8_t *__restrict__ sign,
+                                  const int32_t *__restrict__ in_ptr, int32_t *__restrict__ fill,
+                                  int32_t *__restrict__ in_src, int8_t *__restrict__ in_sign)
+{
+    const int64_t m = *d_nsyn;
+    GRID_STRIDE(k, m)
+    {
+        const int32_t t = tgt[k];
+        const int32_t pos = in_ptr[t] + atomicAdd(&fill[t], 1);
+        in_src[pos] = src[k];
+        in_sign[pos] = sign[k];
+    }
+}
+
 // ---------------------------------------------------------------- deletion
 __global__ void delete_needs_kernel(int64_t n, const int32_t *__restrict__ retract_ax,
                                     const int32_t *__restrict__ retract_de, int32_t *vac_ax,
@@ -399,6 +424,7 @@ cudaError_t canonicalise_store(relearn_ctx *c, cudaStream_t st)
                                            which ? c->d_val_alt : c->d_val, bits, c->d_syn_src,
                                            c->d_syn_tgt, c->d_syn_sign);
     note_launch();
+    c->canonical = true;
     return rebuild_views(c, st);
 }
 
@@ -450,7 +476,28 @@ cudaError_t apply_requests(relearn_ctx *c, int32_t *vac_ax, int32_t *vac_de, con
     grow_store_kernel<<<1, 1, 0, st>>>(c->d_i32 + I32_NEW, c->d_i32 + I32_NSYN,
                                        c->d_i64 + I64_NSYN);
     note_launch();
-    return canonicalise_store(c, st);
+    // new synapses sit unsorted at the end of the store until an operation needs the
+    // canonical order (deletion, export); spike delivery only needs rows by target
+    c->canonical = false;
+    return rebuild_in_rows(c, st);
+}
+
+cudaError_t rebuild_in_rows(relearn_ctx *c, cudaStream_t st)
+{
+    cudaError_t e;
+    const int64_t n = c->n;
+    const int32_t *dm = c->d_i32 + I32_NSYN;
+    const unsigned gs = grid_for(c->max_synapses, 256, c->num_sms);
+    int32_t *in_cnt = c->d_tcnt, *fill = c->d_tfill;
+    if ((e = cudaMemsetAsync(in_cnt, 0, (n + 1) * sizeof(int32_t), st))) return e;
+    if ((e = cudaMemsetAsync(fill, 0, (n + 1) * sizeof(int32_t), st))) return e;
+    in_degree_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_tgt, in_cnt);
+    note_launch();
+    if ((e = scan_exclusive(in_cnt, c->d_in_ptr, n + 1, nullptr, nullptr, c->scan, st))) return e;
+    in_scatter_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_syn_tgt, c->d_syn_sign,
+                                          c->d_in_ptr, fill, c->d_in_src, c->d_in_sign);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t delete_synapses(relearn_ctx *c, const relearn_params &p, const int32_t *retract_ax,
@@ -463,6 +510,7 @@ cudaError_t delete_synapses(relearn_ctx *c, const relearn_params &p, const int32
     const int32_t *dm = c->d_i32 + I32_NSYN;
     const unsigned gs = grid_for(c->max_synapses, 256, c->num_sms);
     const unsigned gn = grid_for(n, 256, c->num_sms);
+    if (!c->canonical && (e = canonicalise_store(c, st))) return e;
     delete_needs_kernel<<<gn, 256, 0, st>>>(n, retract_ax, retract_de, vac_ax, vac_de,
                                             c->d_out_ptr, c->d_in_ptr, c->d_need_ax,
                                             c->d_need_de);

@@ -38,7 +38,7 @@ class RelearnError(RuntimeError):
 class relearn_params(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_float), ("theta", ctypes.c_float), ("seed", ctypes.c_uint64),
                 ("step", ctypes.c_uint64), ("flags", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("search_group", ctypes.c_uint32)]
 
 
 class relearn_update_stats(ctypes.Structure):
@@ -48,7 +48,8 @@ class relearn_update_stats(ctypes.Structure):
                 ("ms_search", ctypes.c_float), ("ms_search_kernel", ctypes.c_float),
                 ("ms_accept", ctypes.c_float), ("ms_apply", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("reserved", ctypes.c_int32),
-                ("searches_total", ctypes.c_int64), ("evals_total", ctypes.c_int64)]
+                ("searches_total", ctypes.c_int64), ("evals_total", ctypes.c_int64),
+                ("walk_steps_total", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -168,8 +169,9 @@ def _raise(ctx, status, where):
     raise RelearnError(status, where, msg)
 
 
-def params(sigma, theta, seed, step, flags=0):
-    return relearn_params(float(sigma), float(theta), int(seed), int(step), int(flags), 0)
+def params(sigma, theta, seed, step, flags=0, search_group=0):
+    return relearn_params(float(sigma), float(theta), int(seed), int(step), int(flags),
+                          int(search_group))
 
 
 # ------------------------------------------------------------------ entry points

@@ -110,6 +110,26 @@ def test_search_matches_oracle_4096(theta):
     g.close()
 
 
+def test_results_do_not_depend_on_search_group():
+    """The number of source neurons that walk the tree together is a tuning knob:
+    requests must be bit-identical for every group size."""
+    from paper_2509_26193_gb300 import relearn as R
+    net = workloads.gaussian_clusters(n=40000, clusters=6, side=3000, std=150, seed=33,
+                                      sigma=300.0)
+    got = []
+    for group in (8, 16, 32):
+        g = GpuNet(net)
+        p = R.params(net.sigma, net.theta, net.seed, 5, R.FLAG_DIAG, group)
+        R.relearn_update_connectivity(g.ctx, p, g.vac_ax, g.vac_de, g.type)
+        tgt, acc = g.requests()
+        dg = R.relearn_get_search_diag(g.ctx)
+        got.append((tgt, acc, dg["ln_s0"], dg["evals"]))
+        g.close()
+    for other in got[1:]:
+        for a, b in zip(got[0], other):
+            assert np.array_equal(a, b)
+
+
 def test_accept_apply_match_oracle_replay():
     net = workloads.gaussian_clusters(n=30000, clusters=5, side=2500, std=150, seed=51,
                                       sigma=300.0)
