@@ -55,7 +55,11 @@ typedef struct relearn_ctx relearn_ctx;
  *   step      update index (< 2^32), part of every Philox counter.
  *   flags     RELEARN_FLAG_* bits.
  *   search_group  tuning only (results do not depend on it): how many source neurons walk
- *             the octree together in the search kernel, 8, 16 or 32; 0 = library default. */
+ *             the octree together in the search kernel: 1, 8, 16 or 32 for a fixed width;
+ *             0 = chosen per warp from how close its sources are (default);
+ *             1000 + 100 * d32 + d8 (d32, d8 = 0..10) = chosen per warp: 32 together when
+ *             they share a cell of depth >= d32, else 8 together when they share a cell of
+ *             depth >= d8, else one by one. */
 typedef struct {
     float sigma;
     float theta;

@@ -71,6 +71,13 @@ struct __align__(32) Node {
 
 constexpr int kMaxDepth = 10;
 
+// Number of leading octal digits (octree levels) two Morton codes share; 10 when equal.
+__device__ __forceinline__ int morton_common_digits(uint32_t a, uint32_t b)
+{
+    const uint32_t d = a ^ b;
+    return d ? (__clz(d) - 2) / 3 : 10;
+}
+
 // The acceptance test of a node at depth d, d^2 > thr0 / 4^d, is evaluated as
 // d^2 * 4^d > thr0 by adding d << 24 to the bits of d^2 (2d to its exponent;
 // exact, as is the division of thr0 by 4^d), and comparing the result as an

@@ -35,7 +35,11 @@ namespace {
 constexpr int kCkStride = 128; // warp steps between checkpoints
 constexpr int kMaxCk = 128;    // checkpoints kept per lane (later steps reuse the last one)
 constexpr float kTiny = 8.673617e-19f; // 2^-60
-constexpr uint32_t kDefaultGroup = 16; // lanes per union walk unless params.search_group says
+// Walk width per warp (see bh_search_kernel): the 32 sources of a warp share one walk
+// when they lie in one cell of depth >= kSpreadDepth, else groups of 8 do when each of
+// those fits such a cell, else every lane walks alone.
+constexpr int kSpreadDepth = 4;
+constexpr int kSpreadDepth8 = 4;
 
 // A node of depth d is accepted iff d^2 > thr0 / 4^d, thr0 = (root length / theta)^2
 // rounded to FP32 (see NodeTopo::shift). theta = 0 accepts no inner node.
@@ -111,6 +115,7 @@ struct SearchArgs {
     const float4 *__restrict__ pos;
     const int32_t *__restrict__ perm;
     const int32_t *__restrict__ act_src;
+    const uint32_t *__restrict__ codes;
     const int32_t *__restrict__ leaf_of;
     const int32_t *__restrict__ vac_ax;
     const int32_t *__restrict__ qoff_o;
@@ -126,6 +131,9 @@ struct SearchArgs {
     int32_t *diag_restarts;
     uint64_t seed;
     uint32_t step;
+    int forced_group; // 0 = choose per warp
+    int spread_depth;  // a union of 32 needs all sources in one cell this deep
+    int spread_depth8; // else a union of 8 needs its sources in one cell this deep
 };
 
 struct WalkOut {
@@ -185,9 +193,10 @@ __device__ __forceinline__ WalkOut walk(const Node *__restrict__ nodes, int32_t 
     return o;
 }
 
-// G = lanes per union walk (8, 16 or 32). A warp runs 32 / G independent walks,
-// so 32 / G node loads are in flight per step, and each union covers fewer sources.
-template <int G>
+// G = lanes per union walk (1, 8, 16 or 32), chosen per warp task from the spread of
+// its 32 sources (a union is only worth walking when its sources are close: far-apart
+// sources share few nodes and most lanes would idle). A warp runs 32 / G independent
+// walks, 32 / G node loads in flight per step. Results do not depend on G.
 __global__ void __launch_bounds__(256) bh_search_kernel(SearchArgs a)
 {
     const uint32_t thr0 = __ldg(&a.sc->thr0);
@@ -195,8 +204,6 @@ __global__ void __launch_bounds__(256) bh_search_kernel(SearchArgs a)
     const int32_t A = *a.d_A;
     const int32_t root_end = __ldg(&a.nodes[0].t.escape);
     const int lane = threadIdx.x & 31;
-    const uint32_t gmask =
-        G == 32 ? 0xffffffffu : (((1u << (G & 31)) - 1u) << (lane & ~(G - 1)));
     int64_t my_evals = 0, my_steps = 0;
     int32_t ckp[kMaxCk];
     float ckc[kMaxCk];
@@ -212,6 +219,27 @@ __global__ void __launch_bounds__(256) bh_search_kernel(SearchArgs a)
         const float3 x = make_float3(xp.x, xp.y, xp.z);
         const int32_t self_node = live ? a.leaf_of[s] : -1;
 
+        // ---- walk width: Morton codes are sorted, so the first and last code of a
+        // range bound the cell that holds all of it
+        int G = a.forced_group;
+        if (G == 0) {
+            const int last = min(A - 1 - nb, 31);
+            uint32_t code = live ? a.codes[s] : 0u;
+            code = __shfl_sync(0xffffffffu, code, live ? lane : last);
+            const uint32_t c0 = __shfl_sync(0xffffffffu, code, 0);
+            const uint32_t c31 = __shfl_sync(0xffffffffu, code, 31);
+            if (morton_common_digits(c0, c31) >= a.spread_depth) {
+                G = 32;
+            } else {
+                const uint32_t f = __shfl_sync(0xffffffffu, code, lane & ~7);
+                const uint32_t l = __shfl_sync(0xffffffffu, code, lane | 7);
+                const int cp8 = __reduce_min_sync(0xffffffffu, morton_common_digits(f, l));
+                G = cp8 >= a.spread_depth8 ? 8 : 1;
+            }
+        }
+        const uint32_t gmask =
+            G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+
         // ---- pass 1: union of the G root frontiers of this lane's group
         float k2sh = 0.0f, S = 0.0f;
         int32_t own = 0, nck = 0;
@@ -220,7 +248,7 @@ __global__ void __launch_bounds__(256) bh_search_kernel(SearchArgs a)
             float cum = 0.0f;
             own = 0;
             nck = 0;
-            if constexpr (G == 32) {
+            if (G == 32) {
                 // one walk per warp: every lane steps together, no group masks
                 while (p < root_end) {
                     if (nck < kMaxCk) {
@@ -272,7 +300,7 @@ __global__ void __launch_bounds__(256) bh_search_kernel(SearchArgs a)
                     if (run) p = down ? p + 1 : max(t.x, p + 1);
                 }
             }
-            my_steps += steps;
+            if ((lane & (G - 1)) == 0) my_steps += steps; // one count per walk
             S = cum;
             // every term underflowed: redo with the exponents shifted by the nearest d^2
             const bool redo = live && cum < kTiny;
@@ -361,9 +389,9 @@ __global__ void __launch_bounds__(256) bh_search_kernel(SearchArgs a)
     if (lane == 0 && my_evals)
         atomicAdd(reinterpret_cast<unsigned long long *>(a.evals_total),
                   (unsigned long long)my_evals);
-    if (lane == 0 && my_steps) // every lane of a group counted the group's steps
+    if (lane == 0 && my_steps)
         atomicAdd(reinterpret_cast<unsigned long long *>(a.steps_total),
-                  (unsigned long long)(my_steps / G));
+                  (unsigned long long)my_steps);
 }
 
 inline unsigned grid_for(int64_t n, int threads, int num_sms)
@@ -416,6 +444,7 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     a.pos = c->d_pos;
     a.perm = c->d_perm;
     a.act_src = c->d_act_src;
+    a.codes = c->d_codes;
     a.leaf_of = c->d_leaf;
     a.vac_ax = vac_ax;
     a.qoff_o = c->d_qoff_o;
@@ -432,10 +461,12 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     a.diag_restarts = diag ? c->d_diag_restarts : nullptr;
     a.seed = p.seed;
     a.step = (uint32_t)p.step;
-    const uint32_t group = p.search_group ? p.search_group : kDefaultGroup;
-    void (*kern)(SearchArgs) = group == 8    ? bh_search_kernel<8>
-                               : group == 16 ? bh_search_kernel<16>
-                                             : bh_search_kernel<32>;
+    // search_group: 0 = per-warp choice, 1/8/16/32 = fixed width,
+    // 1000 + 100 * d32 + d8 = per-warp choice with spread depths d32, d8 (tuning)
+    a.forced_group = p.search_group < 1000 ? (int)p.search_group : 0;
+    a.spread_depth = p.search_group >= 1000 ? (int)((p.search_group - 1000) / 100) : kSpreadDepth;
+    a.spread_depth8 = p.search_group >= 1000 ? (int)((p.search_group - 1000) % 100) : kSpreadDepth8;
+    void (*kern)(SearchArgs) = bh_search_kernel;
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0))) return e;
     if (per_sm < 1) per_sm = 1;

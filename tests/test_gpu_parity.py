@@ -117,7 +117,7 @@ def test_results_do_not_depend_on_search_group():
     net = workloads.gaussian_clusters(n=40000, clusters=6, side=3000, std=150, seed=33,
                                       sigma=300.0)
     got = []
-    for group in (8, 16, 32):
+    for group in (1, 8, 16, 32, 0, 1503, 1300):
         g = GpuNet(net)
         p = R.params(net.sigma, net.theta, net.seed, 5, R.FLAG_DIAG, group)
         R.relearn_update_connectivity(g.ctx, p, g.vac_ax, g.vac_de, g.type)
