@@ -197,7 +197,10 @@ __device__ __forceinline__ WalkOut walk(const Node *__restrict__ nodes, int32_t 
 // its 32 sources (a union is only worth walking when its sources are close: far-apart
 // sources share few nodes and most lanes would idle). A warp runs 32 / G independent
 // walks, 32 / G node loads in flight per step. Results do not depend on G.
-__global__ void __launch_bounds__(256) bh_search_kernel(SearchArgs a)
+#ifndef RELEARN_SEARCH_MIN_BLOCKS
+#define RELEARN_SEARCH_MIN_BLOCKS 6 // 40 registers: 6 blocks of 256 threads per SM
+#endif
+__global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kernel(SearchArgs a)
 {
     const uint32_t thr0 = __ldg(&a.sc->thr0);
     const float k2 = __ldg(&a.sc->k2);
