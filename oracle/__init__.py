@@ -91,6 +91,7 @@ def lib():
                 "orc_apply": (_I64, [_I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P, _P]),
                 "orc_delete": (_I64, [_I64, _P, _P, _P, _P, _U64, _U64, _P, _P, _P, _P]),
                 "orc_deliver_spikes": (None, [_I64, _I64, _P, _P, _P, _P, _P]),
+                "orc_deliver_rates": (None, [_I64, _I64, _P, _P, _P, _P, _U64, _U64, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -290,6 +291,15 @@ def deliver_spikes(n, syn: Synapses, spiked):
     out = np.zeros(n, np.int32)
     lib().orc_deliver_spikes(n, syn.count, _p(syn.src), _p(syn.tgt), _p(syn.sign), _p(spiked),
                              _p(out))
+    return out
+
+
+def deliver_rates(n, syn: Synapses, rate, seed, step):
+    """Firing-rate delivery (Sec. IV-B): Bernoulli(rate[s]) per (s, t, step)."""
+    rate = _c(rate, np.float32)
+    out = np.zeros(n, np.int32)
+    lib().orc_deliver_rates(n, syn.count, _p(syn.src), _p(syn.tgt), _p(syn.sign), _p(rate),
+                            seed, step, _p(out))
     return out
 
 

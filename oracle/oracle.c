@@ -19,6 +19,7 @@
  *   acceptance + apply ...... Sec. III-A "Update of synapses", second sub-phase
  *   deletion ................ Sec. III-A "Update of synapses", first sub-phase
  *   spike delivery .......... Sec. III-A "Update of electrical activity"
+ *   firing-rate delivery .... Sec. IV-B "Approximation of firing rates"
  *
  * Readings where the paper is silent (restated at each function):
  *   R1  domain = bounding box of the positions unless a box is given (anisotropic cells)
@@ -39,6 +40,9 @@
  *       priority per row slot; a synapse picked by both ends is broken once and
  *       returns no vacancy
  *   R12 duplicate (src, tgt) synapses are allowed and counted
+ *   R13 firing-rate delivery: the receiver t decides once per step and per source s
+ *       whether s spiked, w = philox({s, t, step, 4}, seed).x, spiked iff
+ *       w < rate[s] * 2^32 (exact in FP64); every synapse s -> t then carries that spike
  *
  * Every function here has a pin in the CPU test suite (tests/test_oracle_*.py).
  */
@@ -927,4 +931,20 @@ void orc_deliver_spikes(int64_t n, int64_t nsyn, const int32_t *s_src, const int
     for (int64_t t = 0; t < n; ++t) input[t] = 0;
     for (int64_t k = 0; k < nsyn; ++k)
         if (spiked[s_src[k]]) input[s_tgt[k]] += s_sign[k];
+}
+
+/* ------------------------------------------------------------------------- */
+/* Firing-rate delivery (Sec. IV-B "Approximation of firing rates"): instead of
+ * receiving spikes, a neuron uses the sender's firing frequency and a PRNG to
+ * decide whether the sender spiked in this step (R13). */
+/* ------------------------------------------------------------------------- */
+void orc_deliver_rates(int64_t n, int64_t nsyn, const int32_t *s_src, const int32_t *s_tgt,
+                       const int8_t *s_sign, const float *rate, uint64_t seed, uint64_t step,
+                       int32_t *input)
+{
+    for (int64_t t = 0; t < n; ++t) input[t] = 0;
+    for (int64_t k = 0; k < nsyn; ++k) {
+        uint32_t w = philox_x((uint32_t)s_src[k], (uint32_t)s_tgt[k], (uint32_t)step, 4u, seed);
+        if ((double)w < (double)rate[s_src[k]] * 4294967296.0) input[s_tgt[k]] += s_sign[k];
+    }
 }

@@ -158,3 +158,40 @@ def test_spike_delivery_is_signed_adjacency_product(orc):
     s, d, g = syn.arrays()
     A = sparse.coo_matrix((g.astype(np.int64), (d, s)), shape=(n, n)).tocsr()
     assert np.array_equal(got, A @ spiked.astype(np.int64))
+
+
+# --------------------------------------------------- firing-rate delivery
+def test_rate_delivery_extremes_equal_spike_delivery(orc):
+    # rate 1 = always spiked, rate 0 = never: exactly the spike delivery of those flags
+    rng = np.random.default_rng(12)
+    n = 300
+    types = (rng.random(n) < 0.2).astype(np.uint8)
+    pairs = [(int(a), int(b)) for a, b in rng.integers(0, n, (3000, 2))]
+    syn = _store(orc, pairs, n, types)
+    spiked = (rng.random(n) < 0.3).astype(np.uint8)
+    rate = spiked.astype(np.float32)
+    for step in range(3):
+        assert np.array_equal(orc.deliver_rates(n, syn, rate, 5, step),
+                              orc.deliver_spikes(n, syn, spiked))
+
+
+def test_rate_delivery_mean_is_expected_input(orc):
+    # E[input[t]] = sum over synapses s -> t of sign * rate[s]
+    rng = np.random.default_rng(13)
+    n = 50
+    types = (rng.random(n) < 0.3).astype(np.uint8)
+    pairs = [(int(a), int(b)) for a, b in rng.integers(0, n, (400, 2))]
+    syn = _store(orc, pairs, n, types)
+    rate = rng.uniform(0.0, 0.6, n).astype(np.float32)
+    steps = 4000
+    acc = np.zeros(n)
+    for step in range(steps):
+        acc += orc.deliver_rates(n, syn, rate, 9, step)
+    s, d, g = syn.arrays()
+    want = np.zeros(n)
+    np.add.at(want, d, g * rate[s].astype(np.float64))
+    var = np.zeros(n)
+    np.add.at(var, d, (rate[s] * (1 - rate[s])).astype(np.float64))
+    # duplicates of one (s, t) pair share the draw: bound their covariance generously
+    sd = np.sqrt(np.maximum(var, 1e-9) * 4 / steps)
+    assert np.all(np.abs(acc / steps - want) < 5 * sd + 1e-9)
