@@ -170,6 +170,16 @@ relearn_status relearn_delete_synapses(relearn_ctx *ctx, const relearn_params *p
 relearn_status relearn_deliver_spikes(relearn_ctx *ctx, const uint8_t *spiked, int32_t *input,
                                       void *stream);
 
+/* Firing-rate-approximated spike delivery (Sec. IV-B, "Approximation of firing rates"):
+ * instead of receiving spikes, neuron t decides once per step and per presynaptic
+ * neuron s whether s spiked, from s's firing rate and a PRNG:
+ *   spiked(s, t) = Philox4x32-10({s, t, step, 4}, seed).x < rate[s] * 2^32,
+ *   input[t] = sum over synapses s -> t of sign(s) * spiked(s, t)   (duplicates count).
+ *   rate   device float[n], probability of a spike per step (values <= 0 never, >= 1
+ *          always spike).  input  device int32[n], written.  step < 2^32. */
+relearn_status relearn_deliver_rates(relearn_ctx *ctx, const float *rate, uint64_t seed,
+                                     uint64_t step, int32_t *input, void *stream);
+
 /* Copy the synapse store to host arrays in canonical order (by source, then target).
  * `count` (host) receives the number stored; src/tgt/sign may be NULL to query only the
  * count, else they must hold `capacity` entries (INVALID_ARG if too small).

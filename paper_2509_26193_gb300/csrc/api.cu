@@ -373,6 +373,21 @@ relearn_status relearn_deliver_spikes(relearn_ctx *c, const uint8_t *spiked, int
     return RELEARN_OK;
 }
 
+relearn_status relearn_deliver_rates(relearn_ctx *c, const float *rate, uint64_t seed,
+                                     uint64_t step, int32_t *input, void *stream)
+{
+    if (!c) return RELEARN_ERR_INVALID_ARG;
+    if (!c->built) return fail(c, RELEARN_ERR_STATE, "deliver_rates before build_octree");
+    if (!rate || !input) return fail(c, RELEARN_ERR_INVALID_ARG, "deliver_rates: NULL array");
+    if (step > 0xffffffffull) return fail(c, RELEARN_ERR_INVALID_ARG, "deliver_rates: step");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(c, RELEARN_ERR_CUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    CK(deliver_rates(c, rate, seed, (uint32_t)step, input, st), "deliver rates");
+    return RELEARN_OK;
+}
+
 relearn_status relearn_get_synapses(relearn_ctx *c, int64_t capacity, int64_t *count,
                                     int32_t *src, int32_t *tgt, int8_t *sign)
 {

@@ -164,5 +164,7 @@ cudaError_t delete_synapses(relearn_ctx *c, const relearn_params &p, const int32
 cudaError_t deliver_spikes(relearn_ctx *c, const uint8_t *spiked, int32_t *input,
                            cudaStream_t st);
 cudaError_t canonicalise_store(relearn_ctx *c, cudaStream_t st);
+cudaError_t deliver_rates(relearn_ctx *c, const float *rate, uint64_t seed, uint32_t step,
+                          int32_t *input, cudaStream_t st);
 
 } // namespace rl

@@ -17,10 +17,14 @@
 // order of the cumulative draw. Every kCkStride warp steps each lane stores a
 // checkpoint (its next own node, its running sum).
 //
-// Draw (pass 2): u * S is located between two checkpoints by binary search and
-// the lane walks its own candidates from there, repeating pass 1's arithmetic
-// bit for bit (explicit round-to-nearest intrinsics), until the running sum
-// exceeds u * S. An inner node that is drawn restarts the search from itself;
+// Sums: each lane accumulates its own terms in FP32 with Kahan compensation (the
+// running total is sum - c, accurate to a few ulp whatever the number of terms);
+// S, the root-level normaliser, is formed in FP64 from (sum, c).
+//
+// Draw (pass 2): u * S is located between two checkpoints by binary search and the
+// lane walks its own candidates from there, repeating pass 1's compensated
+// arithmetic bit for bit (explicit round-to-nearest intrinsics), until its running
+// total exceeds u * S. An inner node that is drawn restarts the search from itself;
 // restart frontiers are small and are walked per lane (sum, then find).
 //
 // Attraction a = count * 2^(-k2 d^2 + k2sh), k2 = log2(e) / sigma^2. k2sh = 0
@@ -193,6 +197,42 @@ __device__ __forceinline__ WalkOut walk(const Node *__restrict__ nodes, int32_t 
     return o;
 }
 
+// Kahan step: sum + a with the rounding error carried in c (explicit round-to-
+// nearest operations, so every pass reproduces the same bits).
+__device__ __forceinline__ void kahan_add(float &sum, float &c, float a)
+{
+    const float y = __fsub_rn(a, c);
+    const float t = __fadd_rn(sum, y);
+    c = __fsub_rn(__fsub_rn(t, sum), y);
+    sum = t;
+}
+
+// Draw on the root frontier from a checkpoint: the lane's own walk with pass 1's
+// compensated arithmetic; returns the first candidate whose running total
+// (sum - c) exceeds target, else the last candidate with weight, else -1.
+__device__ __forceinline__ int32_t find_root(const Node *__restrict__ nodes, int32_t p,
+                                             int32_t end, float cum, float comp, float3 x,
+                                             int32_t self_node, uint32_t thr0, float k2,
+                                             float k2sh, float target)
+{
+    int32_t pick = -1;
+    while (p < end) {
+        const float4 g = __ldg(reinterpret_cast<const float4 *>(&nodes[p].g));
+        const int2 t = __ldg(reinterpret_cast<const int2 *>(&nodes[p].t));
+        const float d2 = dist2(x, g);
+        const bool has = g.w > 0.0f;
+        const bool acc = has && (__float_as_uint(d2) + (uint32_t)t.y > thr0);
+        if (acc && p != self_node) {
+            const float a = attraction(g.w, d2, k2, k2sh);
+            kahan_add(cum, comp, a);
+            if (a > 0.0f) pick = p;
+            if (__fsub_rn(cum, comp) > target) return p;
+        }
+        p = (has && !acc) ? p + 1 : max(t.x, p + 1);
+    }
+    return pick;
+}
+
 // G = lanes per union walk (1, 8, 16 or 32), chosen per warp task from the spread of
 // its 32 sources (a union is only worth walking when its sources are close: far-apart
 // sources share few nodes and most lanes would idle). A warp runs 32 / G independent
@@ -209,7 +249,8 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
     const int lane = threadIdx.x & 31;
     int64_t my_evals = 0, my_steps = 0;
     int32_t ckp[kMaxCk];
-    float ckc[kMaxCk];
+    float ckc[kMaxCk];  // compensated running sum at each checkpoint
+    float ckk[kMaxCk];  // its compensation term
     for (;;) {
         int32_t nb = 0;
         if (lane == 0) nb = atomicAdd(a.work, 32);
@@ -244,11 +285,12 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
             G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
 
         // ---- pass 1: union of the G root frontiers of this lane's group
-        float k2sh = 0.0f, S = 0.0f;
+        float k2sh = 0.0f;
+        double S = 0.0; // the root-level normaliser, FP64
         int32_t own = 0, nck = 0;
         for (int attempt = 0; attempt < 2; ++attempt) {
             int32_t p = 1, skip = live ? 0 : 0x7fffffff, steps = 0;
-            float cum = 0.0f;
+            float cum = 0.0f, comp = 0.0f; // Kahan sum and compensation
             own = 0;
             nck = 0;
             if (G == 32) {
@@ -257,6 +299,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                     if (nck < kMaxCk) {
                         ckp[nck] = max(p, skip);
                         ckc[nck] = cum;
+                        ckk[nck] = comp;
                         ++nck;
                     }
 #pragma unroll 1
@@ -270,7 +313,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                         if (on && pass) {
                             skip = t.x;
                             if (p != self_node)
-                                cum = __fadd_rn(cum, attraction(g.w, d2, k2, k2sh));
+                                kahan_add(cum, comp, attraction(g.w, d2, k2, k2sh));
                         }
                         p = __any_sync(0xffffffffu, on && !pass) ? p + 1 : max(t.x, p + 1);
                         ++steps;
@@ -285,6 +328,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                         if ((steps & (kCkStride - 1)) == 0 && nck < kMaxCk) {
                             ckp[nck] = max(p, skip);
                             ckc[nck] = cum;
+                            ckk[nck] = comp;
                             ++nck;
                         }
                         ++steps;
@@ -297,16 +341,17 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                     own += on ? 1 : 0;
                     if (on && pass) {
                         skip = t.x;
-                        if (p != self_node) cum = __fadd_rn(cum, attraction(g.w, d2, k2, k2sh));
+                        if (p != self_node)
+                            kahan_add(cum, comp, attraction(g.w, d2, k2, k2sh));
                     }
                     const uint32_t down = __ballot_sync(0xffffffffu, on && !pass) & gmask;
                     if (run) p = down ? p + 1 : max(t.x, p + 1);
                 }
             }
             if ((lane & (G - 1)) == 0) my_steps += steps; // one count per walk
-            S = cum;
+            S = (double)cum - (double)comp;
             // every term underflowed: redo with the exponents shifted by the nearest d^2
-            const bool redo = live && cum < kTiny;
+            const bool redo = live && S < (double)kTiny;
             if (!__any_sync(0xffffffffu, redo)) break;
             if (redo) {
                 const WalkOut w = walk<false>(a.nodes, 1, root_end, 0.0f, x, self_node, thr0, k2,
@@ -321,28 +366,26 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
         const int32_t i = a.perm[s];
         const int32_t nq = max(a.vac_ax[i], 0);
         const int32_t qbase = a.qoff_o[i];
-        const double lns0 =
-            S > 0.0f ? log((double)S) - (double)k2sh * 0.6931471805599453
-                     : -__longlong_as_double(0x7ff0000000000000LL);
+        const double lns0 = S > 0.0 ? log(S) - (double)k2sh * 0.6931471805599453
+                                    : -__longlong_as_double(0x7ff0000000000000LL);
         for (int32_t e = 0; e < nq; ++e) {
             int32_t result = -1, evals = own, draws = 0;
-            if (S > 0.0f) {
+            if (S > 0.0) {
                 uint32_t u = philox_x((uint32_t)i, a.step, (uint32_t)e << 8, 0u, a.seed);
-                float target = (float)((double)u * 2.3283064365386963e-10 * (double)S);
-                int lo = 0, hi = nck - 1; // last checkpoint whose running sum <= target
+                const double tgt = (double)u * 2.3283064365386963e-10 * S;
+                int lo = 0, hi = nck - 1; // last checkpoint whose sum <= u * S
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (ckc[mid] <= target)
+                    if ((double)ckc[mid] - (double)ckk[mid] <= tgt)
                         lo = mid;
                     else
                         hi = mid - 1;
                 }
-                WalkOut w = walk<true>(a.nodes, ckp[lo], root_end, ckc[lo], x, self_node, thr0,
-                                       k2, k2sh, target);
-                if (w.pick < 0) // u * S rounded up to S past the last weighted candidate
-                    w = walk<true>(a.nodes, 1, root_end, 0.0f, x, self_node, thr0, k2, k2sh,
-                                   __int_as_float(0x7f800000));
-                int32_t k = w.pick;
+                int32_t k = find_root(a.nodes, ckp[lo], root_end, ckc[lo], ckk[lo], x, self_node,
+                                      thr0, k2, k2sh, (float)tgt);
+                if (k < 0) // u * S rounded up to S past the last weighted candidate
+                    k = find_root(a.nodes, 1, root_end, 0.0f, 0.0f, x, self_node, thr0, k2, k2sh,
+                                  __int_as_float(0x7f800000));
                 draws = 1;
                 while (k >= 0 && draws < 24) {
                     const int4 tk = __ldg(reinterpret_cast<const int4 *>(&a.nodes[k].t));
@@ -369,7 +412,8 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                     u = philox_x((uint32_t)i, a.step,
                                  ((uint32_t)e << 8) | (uint32_t)depth_of((uint32_t)tk.y), 0u,
                                  a.seed);
-                    target = (float)((double)u * 2.3283064365386963e-10 * (double)w1.sum);
+                    const float target =
+                        (float)((double)u * 2.3283064365386963e-10 * (double)w1.sum);
                     k = walk<true>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2, sh, target)
                             .pick;
                     ++draws;

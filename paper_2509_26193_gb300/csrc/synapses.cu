@@ -381,7 +381,37 @@ __global__ void spikes_kernel(int64_t n, const int32_t *__restrict__ in_ptr,
     }
 }
 
+// Firing-rate delivery (Sec. IV-B): the receiver t decides once per step and per
+// source s whether s spiked, spiked iff philox({s, t, step, 4}).x < rate[s] * 2^32
+// (an exact FP64 comparison); duplicates of (s, t) share that decision.
+__global__ void rates_kernel(int64_t n, const int32_t *__restrict__ in_ptr,
+                             const int32_t *__restrict__ in_src,
+                             const int8_t *__restrict__ in_sign, const float *__restrict__ rate,
+                             uint64_t seed, uint32_t step, int32_t *__restrict__ input)
+{
+    GRID_STRIDE(t, n)
+    {
+        int32_t acc = 0;
+        const int32_t b = in_ptr[t], e = in_ptr[t + 1];
+        for (int32_t k = b; k < e; ++k) {
+            const int32_t s = in_src[k];
+            const uint32_t w = philox_x((uint32_t)s, (uint32_t)t, step, 4u, seed);
+            if ((double)w < (double)rate[s] * 4294967296.0) acc += in_sign[k];
+        }
+        input[t] = acc;
+    }
+}
+
 } // namespace
+
+cudaError_t deliver_rates(relearn_ctx *c, const float *rate, uint64_t seed, uint32_t step,
+                          int32_t *input, cudaStream_t st)
+{
+    rates_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(
+        c->n, c->d_in_ptr, c->d_in_src, c->d_in_sign, rate, seed, step, input);
+    note_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t accept_requests(relearn_ctx *c, const relearn_params &p, const int32_t *vac_de,
                             cudaStream_t st)

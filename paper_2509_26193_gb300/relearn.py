@@ -66,6 +66,7 @@ _SIGS = {
     "relearn_delete_synapses": [_P, ctypes.POINTER(relearn_params), _P, _P, _P, _P,
                                 ctypes.POINTER(_I64), _P],
     "relearn_deliver_spikes": [_P, _P, _P, _P],
+    "relearn_deliver_rates": [_P, _P, ctypes.c_uint64, ctypes.c_uint64, _P, _P],
     "relearn_get_synapses": [_P, _I64, ctypes.POINTER(_I64), _P, _P, _P],
     "relearn_set_synapses": [_P, _I64, _P, _P, _P],
     "relearn_get_requests": [_P, _I64, ctypes.POINTER(_I64), _P, _P],
@@ -245,6 +246,15 @@ def relearn_deliver_spikes(ctx, spiked, out, stream=None):
     o = _dev_ptr(out, torch.int32, n, "input")
     st = lib().relearn_deliver_spikes(ctx.handle, s, o, _stream(stream))
     _raise(ctx, st, "relearn_deliver_spikes")
+
+
+def relearn_deliver_rates(ctx, rate, seed, step, out, stream=None):
+    torch = _torch()
+    n = ctx.n
+    r = _dev_ptr(rate, torch.float32, n, "rate")
+    o = _dev_ptr(out, torch.int32, n, "input")
+    st = lib().relearn_deliver_rates(ctx.handle, r, int(seed), int(step), o, _stream(stream))
+    _raise(ctx, st, "relearn_deliver_rates")
 
 
 def relearn_get_synapses(ctx):

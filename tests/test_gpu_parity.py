@@ -197,6 +197,14 @@ def test_multistep_update_delete_spikes():
     out = torch.zeros(net.n, dtype=torch.int32, device="cuda")
     R.relearn_deliver_spikes(g.ctx, dev(spk), out)
     assert np.array_equal(out.cpu().numpy(), oracle.deliver_spikes(net.n, syn, spk))
+    # firing-rate delivery (Sec. IV-B) on the same store, three steps
+    rate = np.random.default_rng(3).uniform(0.0, 0.3, net.n).astype(np.float32)
+    rate[:100] = 0.0
+    rate[100:200] = 1.0
+    for step in (0, 1, 2 ** 31 + 5):
+        R.relearn_deliver_rates(g.ctx, dev(rate), net.seed, step, out)
+        assert np.array_equal(out.cpu().numpy(),
+                              oracle.deliver_rates(net.n, syn, rate, net.seed, step))
     g.close()
 
 
@@ -299,3 +307,35 @@ def test_checkpoint_resume_is_bit_identical():
         assert np.array_equal(x, y)
     a.close()
     b.close()
+
+
+def test_cortical_slab_2p24_sampled():
+    """2^24 neurons in a 10-layer slab (octree rebuilt, one update): sampled searches
+    against the oracle, every acceptance decision bit-exact."""
+    import time
+    net = workloads.cortical_slab()
+    q = int(net.vac_ax.sum())
+    g = GpuNet(net, max_synapses=q + 16)
+    stats = g.update(step=0)
+    assert stats["searches"] == q
+    gt, gacc = g.requests()
+    from paper_2509_26193_gb300 import relearn as R
+    dg = R.relearn_get_search_diag(g.ctx)
+    g.close()
+    t0 = time.time()
+    t = oracle.Tree(net.x, net.y, net.z)
+    t.reduce(net.vac_de)
+    qi, qe = oracle.queries(net.vac_ax)
+    rng = np.random.default_rng(24)
+    sel = np.sort(rng.choice(q, 2000, replace=False))
+    ot, od = t.search_batch(net.sigma, net.theta, net.seed, 0, qi[sel], qe[sel], threads=16)
+    bad, exempt, exempt_diff = compare_targets(gt[sel], ot, od)
+    assert bad == 0, (bad, exempt, exempt_diff)
+    fin = np.isfinite(od["ln_s0"])
+    assert np.abs(dg["ln_s0"][sel][fin] - od["ln_s0"][fin]).max() < LNS_TOL
+    t.close()
+    oacc = oracle.accept(net.n, qi, qe, gt, net.vac_de, net.seed, 0)
+    assert np.array_equal(gacc, oacc)
+    print(f"slab 2^24: {q} searches, GPU update {stats['ms_total']:.2f} ms "
+          f"(search {stats['ms_search_kernel']:.2f} ms), exempt {exempt}/2000, "
+          f"oracle check {time.time() - t0:.1f} s")
