@@ -72,7 +72,7 @@ void free_all(relearn_ctx *c)
         (void **)&c->d_status,   (void **)&c->d_i64,        (void **)&c->d_i32,
         (void **)&c->d_geom,     (void **)&c->d_sc,         (void **)&c->d_codes,
         (void **)&c->d_codes_alt, (void **)&c->d_perm,      (void **)&c->d_perm_alt,
-        (void **)&c->d_pos,      (void **)&c->d_mask,       (void **)&c->d_base,
+        (void **)&c->d_pos,      (void **)&c->d_posq,       (void **)&c->d_mask,       (void **)&c->d_base,
         (void **)&c->d_nodes,    (void **)&c->d_parent,     (void **)&c->d_nsize,
         (void **)&c->d_leaf,     (void **)&c->d_acc,
         (void **)&c->d_cnt,      (void **)&c->d_act_off,    (void **)&c->d_qoff_o,
@@ -181,6 +181,7 @@ relearn_status relearn_create(relearn_ctx **out, int device, int64_t max_neurons
     A(d_perm, N);
     A(d_perm_alt, N);
     A(d_pos, N);
+    A(d_posq, N);
     A(d_mask, N);
     A(d_base, N + 1);
     A(d_nodes, M);

@@ -26,7 +26,10 @@ struct SortScratch {
 struct Geom {
     float lo[3], hi[3], inv[3];
     float pad;
-    double ext; // longest edge of the domain box
+    double ext;      // longest edge of the domain box
+    double fx_lo[3]; // origin of the fixed-point positions (below every position and lo)
+    double fx_scale; // 2^k: positions are held as round((x - fx_lo) * 2^k) < 2^30
+    double fx_inv;   // 2^-k
 };
 
 // Per-update search constants computed on the device from Geom and params.
@@ -59,6 +62,7 @@ struct relearn_ctx {
     uint32_t *d_codes = nullptr, *d_codes_alt = nullptr; // [n]
     int32_t *d_perm = nullptr, *d_perm_alt = nullptr;    // Morton position -> neuron id
     float4 *d_pos = nullptr;                             // positions in Morton order
+    int4 *d_posq = nullptr;                              // fixed-point positions, Morton order
     uint32_t *d_mask = nullptr;                          // [n] depths of nodes starting here
     int32_t *d_base = nullptr;                           // [n + 1] pre-order index of position
     rl::Node *d_nodes = nullptr;                         // [max_nodes]

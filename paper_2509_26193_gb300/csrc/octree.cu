@@ -86,21 +86,20 @@ struct Box {
 
 // Domain box, FP32 inverse extents (IEEE division, as the quantisation formula
 // states) and the longest edge in FP64.
+// The fixed-point frame of the bottom-up sums covers the box and every position:
+// origin = min(box lo, position min), 2^k chosen so that the largest span is
+// below 2^30 units.
 __global__ void geom_kernel(const uint32_t *d_ord, Box box, Geom *g)
 {
-    float lo[3], hi[3];
+    float lo[3], hi[3], blo[3], bhi[3];
     for (int a = 0; a < 3; ++a) {
-        if (box.given) {
-            lo[a] = box.lo[a];
-            hi[a] = box.hi[a];
-        } else if (d_ord[a] == 0xffffffffu) { // all NaN
-            lo[a] = hi[a] = 0.0f;
-        } else {
-            lo[a] = unordered(d_ord[a]);
-            hi[a] = unordered(d_ord[3 + a]);
-        }
+        const bool any = d_ord[a] != 0xffffffffu; // else every coordinate is NaN
+        blo[a] = any ? unordered(d_ord[a]) : 0.0f;
+        bhi[a] = any ? unordered(d_ord[3 + a]) : 0.0f;
+        lo[a] = box.given ? box.lo[a] : blo[a];
+        hi[a] = box.given ? box.hi[a] : bhi[a];
     }
-    double ext = 0.0;
+    double ext = 0.0, span = 0.0;
     for (int a = 0; a < 3; ++a) {
         g->lo[a] = lo[a];
         g->hi[a] = hi[a];
@@ -108,8 +107,31 @@ __global__ void geom_kernel(const uint32_t *d_ord, Box box, Geom *g)
         g->inv[a] = e > 0.0f ? __fdiv_rn(1.0f, e) : 0.0f;
         double ed = (double)hi[a] - (double)lo[a];
         if (ed > ext) ext = ed;
+        const double o = fmin((double)lo[a], (double)blo[a]);
+        const double top = fmax((double)hi[a], (double)bhi[a]);
+        g->fx_lo[a] = o;
+        if (top - o > span) span = top - o;
     }
     g->ext = ext;
+    int k = 30;
+    if (span > 0.0) k = 29 - ilogb(span); // span * 2^k < 2^30
+    k = max(-60, min(k, 60));
+    g->fx_scale = ldexp(1.0, k);
+    g->fx_inv = ldexp(1.0, -k);
+}
+
+__global__ void fixed_pos_kernel(const float4 *__restrict__ pos, int64_t n,
+                                 const Geom *__restrict__ g, int4 *__restrict__ posq)
+{
+    const double ox = g->fx_lo[0], oy = g->fx_lo[1], oz = g->fx_lo[2], sc = g->fx_scale;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const float4 p = pos[s];
+        // NaN or out-of-range coordinates become 0 (the cast is defined as saturating)
+        posq[s] = make_int4(__double2int_rn(((double)p.x - ox) * sc),
+                            __double2int_rn(((double)p.y - oy) * sc),
+                            __double2int_rn(((double)p.z - oz) * sc), 0);
+    }
 }
 
 // Spread the low 10 bits of v to every third bit.
@@ -291,46 +313,48 @@ __global__ void topo_emit_kernel(const uint32_t *__restrict__ codes, int64_t n,
 // Bottom-up update as prefix sums (Sec. III-B "Division of work": an inner node
 // holds the sum of its children's counts and their count-weighted average
 // position, i.e. the sums over the neurons of its cell). Neurons of a cell are a
-// contiguous Morton range [first, first + size), so with the FP64 exclusive
-// prefix P of w = (c, c x, c y, c z) over Morton order, a node's sums are
-// P[first + size] - P[first]. Counts are exact integers; the cancellation error
-// of a position sum is at most a few ulp of the total (about 1e-5 um on a
-// 2^20-neuron, 10 mm network), far below the FP32 rounding of the centroid.
-struct D4 {
-    double c, x, y, z;
+// contiguous Morton range [first, first + size), so with the exclusive prefix P of
+// w = (c, c xq, c yq, c zq) over Morton order, a node's sums are
+// P[first + size] - P[first]. Positions enter as fixed-point integers
+// xq = round((x - origin) * 2^k) < 2^30 (resolution 2^-k, about 1e-5 um for a
+// 10 mm domain), so every sum is an exact int64: order-independent, no
+// cancellation, and no FP64 in the scan. centroid = origin + (sum / count) * 2^-k.
+struct L4 {
+    long long c, x, y, z;
 };
 
-__device__ __forceinline__ D4 d4_add(D4 a, D4 b) { return D4{a.c + b.c, a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ L4 l4_add(L4 a, L4 b) { return L4{a.c + b.c, a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ L4 l4_sub(L4 a, L4 b) { return L4{a.c - b.c, a.x - b.x, a.y - b.y, a.z - b.z}; }
 
-__device__ __forceinline__ D4 d4_shfl_up(D4 v, int o)
+__device__ __forceinline__ L4 l4_shfl_up(L4 v, int o)
 {
-    return D4{__shfl_up_sync(0xffffffffu, v.c, o), __shfl_up_sync(0xffffffffu, v.x, o),
+    return L4{__shfl_up_sync(0xffffffffu, v.c, o), __shfl_up_sync(0xffffffffu, v.x, o),
               __shfl_up_sync(0xffffffffu, v.y, o), __shfl_up_sync(0xffffffffu, v.z, o)};
 }
 
-// Inclusive block scan of D4 (256 threads); *total = block sum.
-__device__ __forceinline__ D4 d4_block_inclusive(D4 v, D4 *total)
+// Inclusive block scan of L4 (256 threads); *total = block sum.
+__device__ __forceinline__ L4 l4_block_inclusive(L4 v, L4 *total)
 {
-    __shared__ D4 wt[8];
+    __shared__ L4 wt[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        D4 t = d4_shfl_up(v, o);
-        if (lane >= o) v = d4_add(v, t);
+        L4 t = l4_shfl_up(v, o);
+        if (lane >= o) v = l4_add(v, t);
     }
     if (lane == 31) wt[warp] = v;
     __syncthreads();
     if (warp == 0) {
-        D4 w = lane < 8 ? wt[lane] : D4{0, 0, 0, 0};
+        L4 w = lane < 8 ? wt[lane] : L4{0, 0, 0, 0};
 #pragma unroll
         for (int o = 1; o < 8; o <<= 1) {
-            D4 t = d4_shfl_up(w, o);
-            if (lane >= o) w = d4_add(w, t);
+            L4 t = l4_shfl_up(w, o);
+            if (lane >= o) w = l4_add(w, t);
         }
         if (lane < 8) wt[lane] = w;
     }
     __syncthreads();
-    if (warp > 0) v = d4_add(v, wt[warp - 1]);
+    if (warp > 0) v = l4_add(v, wt[warp - 1]);
     *total = wt[7];
     __syncthreads();
     return v;
@@ -339,50 +363,52 @@ __device__ __forceinline__ D4 d4_block_inclusive(D4 v, D4 *total)
 constexpr int kRedItems = 4;
 constexpr int kRedTile = 256 * kRedItems;
 
-// Leaf geometry plus w of Morton position s.
-__device__ __forceinline__ D4 leaf_weight(Node *nodes, const int32_t *leaf_of,
+// Leaf geometry (optionally written) plus w of Morton position s.
+__device__ __forceinline__ L4 leaf_weight(Node *nodes, const int32_t *leaf_of,
                                           const int32_t *perm, const float4 *pos,
-                                          const int32_t *vac_de, int64_t s, bool write_leaf)
+                                          const int4 *posq, const int32_t *vac_de, int64_t s,
+                                          bool write_leaf)
 {
     int32_t c = vac_de[perm[s]];
     if (c < 0) c = 0;
-    const float4 p = pos[s];
     if (write_leaf) {
+        const float4 p = pos[s];
         const int32_t v = leaf_of[s];
         nodes[v].g = c > 0 ? NodeGeo{p.x, p.y, p.z, (float)c} : NodeGeo{0.f, 0.f, 0.f, 0.f};
         nodes[v].t.icount = c;
     }
-    const double dc = (double)c;
-    return D4{dc, dc * (double)p.x, dc * (double)p.y, dc * (double)p.z};
+    const int4 q = posq[s];
+    const long long lc = c;
+    return L4{lc, lc * q.x, lc * q.y, lc * q.z};
 }
 
 __global__ void __launch_bounds__(256)
     reduce_sums_kernel(Node *nodes, const int32_t *__restrict__ leaf_of,
                        const int32_t *__restrict__ perm, const float4 *__restrict__ pos,
-                       const int32_t *__restrict__ vac_de, int64_t n, D4 *__restrict__ block_sums)
+                       const int4 *__restrict__ posq, const int32_t *__restrict__ vac_de,
+                       int64_t n, L4 *__restrict__ block_sums)
 {
     const int64_t base = (int64_t)blockIdx.x * kRedTile + (int64_t)threadIdx.x * kRedItems;
-    D4 acc{0, 0, 0, 0};
+    L4 acc{0, 0, 0, 0};
     for (int k = 0; k < kRedItems; ++k)
         if (base + k < n)
-            acc = d4_add(acc, leaf_weight(nodes, leaf_of, perm, pos, vac_de, base + k, true));
-    D4 tot;
-    d4_block_inclusive(acc, &tot);
+            acc = l4_add(acc, leaf_weight(nodes, leaf_of, perm, pos, posq, vac_de, base + k, true));
+    L4 tot;
+    l4_block_inclusive(acc, &tot);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(256) reduce_spine_kernel(D4 *block_sums, int64_t nb, D4 *P,
+__global__ void __launch_bounds__(256) reduce_spine_kernel(L4 *block_sums, int64_t nb, L4 *P,
                                                            int64_t n)
 {
-    D4 carry{0, 0, 0, 0};
+    L4 carry{0, 0, 0, 0};
     for (int64_t c0 = 0; c0 < nb; c0 += 256) {
         const int64_t i = c0 + threadIdx.x;
-        const D4 v = i < nb ? block_sums[i] : D4{0, 0, 0, 0};
-        D4 tot;
-        const D4 inc = d4_block_inclusive(v, &tot);
-        if (i < nb) block_sums[i] = D4{carry.c + inc.c - v.c, carry.x + inc.x - v.x,
-                                      carry.y + inc.y - v.y, carry.z + inc.z - v.z};
-        carry = d4_add(carry, tot);
+        const L4 v = i < nb ? block_sums[i] : L4{0, 0, 0, 0};
+        L4 tot;
+        const L4 inc = l4_block_inclusive(v, &tot);
+        if (i < nb) block_sums[i] = l4_add(carry, l4_sub(inc, v));
+        carry = l4_add(carry, tot);
     }
     if (threadIdx.x == 0) P[n] = carry;
 }
@@ -390,49 +416,48 @@ __global__ void __launch_bounds__(256) reduce_spine_kernel(D4 *block_sums, int64
 __global__ void __launch_bounds__(256)
     reduce_prefix_kernel(Node *nodes, const int32_t *__restrict__ leaf_of,
                          const int32_t *__restrict__ perm, const float4 *__restrict__ pos,
-                         const int32_t *__restrict__ vac_de, int64_t n,
-                         const D4 *__restrict__ block_sums, D4 *__restrict__ P)
+                         const int4 *__restrict__ posq, const int32_t *__restrict__ vac_de,
+                         int64_t n, const L4 *__restrict__ block_sums, L4 *__restrict__ P)
 {
     const int64_t base = (int64_t)blockIdx.x * kRedTile + (int64_t)threadIdx.x * kRedItems;
-    D4 w[kRedItems];
-    D4 acc{0, 0, 0, 0};
+    L4 w[kRedItems];
+    L4 acc{0, 0, 0, 0};
     for (int k = 0; k < kRedItems; ++k) {
-        w[k] = base + k < n ? leaf_weight(nodes, leaf_of, perm, pos, vac_de, base + k, false)
-                            : D4{0, 0, 0, 0};
-        acc = d4_add(acc, w[k]);
+        w[k] = base + k < n ? leaf_weight(nodes, leaf_of, perm, pos, posq, vac_de, base + k, false)
+                            : L4{0, 0, 0, 0};
+        acc = l4_add(acc, w[k]);
     }
-    D4 tot;
-    const D4 inc = d4_block_inclusive(acc, &tot);
-    const D4 off = block_sums[blockIdx.x];
-    D4 run{off.c + inc.c - acc.c, off.x + inc.x - acc.x, off.y + inc.y - acc.y,
-           off.z + inc.z - acc.z};
+    L4 tot;
+    const L4 inc = l4_block_inclusive(acc, &tot);
+    L4 run = l4_add(block_sums[blockIdx.x], l4_sub(inc, acc));
     for (int k = 0; k < kRedItems; ++k) {
         if (base + k < n) P[base + k] = run;
-        run = d4_add(run, w[k]);
+        run = l4_add(run, w[k]);
     }
 }
 
-// Inner nodes: sums from the prefix, FP32 centroid (quotient within 1.5 ulp).
+// Inner nodes: exact sums from the prefix, centroid rounded once to FP32.
 __global__ void reduce_nodes_kernel(Node *__restrict__ nodes, const int32_t *__restrict__ nsize,
-                                    const int64_t *d_num_nodes, const D4 *__restrict__ P)
+                                    const int64_t *d_num_nodes, const L4 *__restrict__ P,
+                                    const Geom *__restrict__ g)
 {
     const int64_t m = *d_num_nodes;
+    const double ox = g->fx_lo[0], oy = g->fx_lo[1], oz = g->fx_lo[2], inv = g->fx_inv;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < m;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int2 t = *reinterpret_cast<const int2 *>(&nodes[v].t);
         if (node_is_leaf((uint32_t)t.y)) continue;
         const int32_t first = nodes[v].t.neuron;
-        const D4 hi = P[first + nsize[v]], lo = P[first];
-        const double sc = hi.c - lo.c;
-        if (sc > 0.0) {
-            const float fc = (float)sc;
-            nodes[v].g = NodeGeo{__fdiv_rn(__double2float_rn(hi.x - lo.x), fc),
-                                 __fdiv_rn(__double2float_rn(hi.y - lo.y), fc),
-                                 __fdiv_rn(__double2float_rn(hi.z - lo.z), fc), fc};
+        const L4 s = l4_sub(P[first + nsize[v]], P[first]);
+        if (s.c > 0) {
+            const double r = inv / (double)s.c;
+            nodes[v].g = NodeGeo{__double2float_rn(ox + (double)s.x * r),
+                                 __double2float_rn(oy + (double)s.y * r),
+                                 __double2float_rn(oz + (double)s.z * r), (float)s.c};
         } else {
             nodes[v].g = NodeGeo{0.f, 0.f, 0.f, 0.f};
         }
-        nodes[v].t.icount = (int32_t)sc;
+        nodes[v].t.icount = (int32_t)s.c;
     }
 }
 
@@ -460,12 +485,10 @@ cudaError_t octree_build(relearn_ctx *c, int64_t n, const float *x, const float 
             box.hi[a] = box_hi[a];
         }
     uint32_t *ord = reinterpret_cast<uint32_t *>(c->d_cnt); // 6 words of scratch
-    if (!box.given) {
-        bbox_init_kernel<<<1, 32, 0, st>>>(ord);
-        note_launch();
-        bbox_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(x, y, z, n, ord);
-        note_launch();
-    }
+    bbox_init_kernel<<<1, 32, 0, st>>>(ord);
+    note_launch();
+    bbox_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(x, y, z, n, ord);
+    note_launch();
     geom_kernel<<<1, 1, 0, st>>>(ord, box, c->d_geom);
     note_launch();
     morton_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(x, y, z, n, c->d_geom,
@@ -486,6 +509,9 @@ cudaError_t octree_build(relearn_ctx *c, int64_t n, const float *x, const float 
     gather_pos_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(x, y, z, c->d_perm, n,
                                                                       c->d_pos);
     note_launch();
+    fixed_pos_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(c->d_pos, n, c->d_geom,
+                                                                     c->d_posq);
+    note_launch();
     if ((e = cudaMemsetAsync(c->d_mask, 0, n * sizeof(uint32_t), st))) return e;
     topo_pairs_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(c->d_codes, n, c->d_mask);
     note_launch();
@@ -504,18 +530,18 @@ cudaError_t octree_reduce(relearn_ctx *c, const int32_t *vac_de, cudaStream_t st
 {
     const int64_t n = c->n;
     const int64_t nb = (n + kRedTile - 1) / kRedTile;
-    D4 *P = reinterpret_cast<D4 *>(c->d_acc);      // n + 1 prefix entries
-    D4 *bsum = P + (n + 1);                          // nb block sums (d_acc holds 2n + 1)
+    L4 *P = reinterpret_cast<L4 *>(c->d_acc);      // n + 1 prefix entries
+    L4 *bsum = P + (n + 1);                          // nb block sums (d_acc holds 2n + 1)
     reduce_sums_kernel<<<(unsigned)nb, 256, 0, st>>>(c->d_nodes, c->d_leaf, c->d_perm, c->d_pos,
-                                                      vac_de, n, bsum);
+                                                      c->d_posq, vac_de, n, bsum);
     note_launch();
     reduce_spine_kernel<<<1, 256, 0, st>>>(bsum, nb, P, n);
     note_launch();
     reduce_prefix_kernel<<<(unsigned)nb, 256, 0, st>>>(c->d_nodes, c->d_leaf, c->d_perm,
-                                                        c->d_pos, vac_de, n, bsum, P);
+                                                        c->d_pos, c->d_posq, vac_de, n, bsum, P);
     note_launch();
     reduce_nodes_kernel<<<grid_for(c->max_nodes, 256, c->num_sms), 256, 0, st>>>(
-        c->d_nodes, c->d_nsize, c->d_i64 + I64_NODES, P);
+        c->d_nodes, c->d_nsize, c->d_i64 + I64_NODES, P, c->d_geom);
     note_launch();
     return cudaGetLastError();
 }
@@ -623,12 +649,10 @@ extern "C" relearn_status relearn_morton_order_noalloc(int64_t n, const float *x
             box.hi[a] = box_hi3[a];
         }
     const unsigned grid = grid_for(n, 256, d.num_sms);
-    if (!box.given) {
-        bbox_init_kernel<<<1, 32, 0, st>>>(ord);
-        note_launch();
-        bbox_kernel<<<grid, 256, 0, st>>>(x, y, z, n, ord);
-        note_launch();
-    }
+    bbox_init_kernel<<<1, 32, 0, st>>>(ord); // geom_kernel reads the bounding box
+    note_launch();
+    bbox_kernel<<<grid, 256, 0, st>>>(x, y, z, n, ord);
+    note_launch();
     geom_kernel<<<1, 1, 0, st>>>(ord, box, geom);
     note_launch();
     morton_kernel<<<grid, 256, 0, st>>>(x, y, z, n, geom, codes, perm);
