@@ -66,6 +66,24 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def search_traffic():
+    """DRAM bytes per search-kernel launch from the committed ncu summary, or None when
+    the kernel sources changed since those counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "bh_search_traffic_gaussian_clusters_2p20.md")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    for f in ("search.cu", "device.cuh", "octree.cu"):
+        with open(os.path.join(ROOT, "paper_2509_26193_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    fields = dict(line.split(": ", 1) for line in open(path).read().splitlines()
+                  if line.startswith(("sources-sha256", "traffic-bytes-per-launch")))
+    if fields.get("sources-sha256", "").strip() != h.hexdigest():
+        return None
+    return int(fields["traffic-bytes-per-launch"])
+
+
 def workload_config(net, theta, extra=None):
     cfg = {"workload": f"gaussian_clusters n={net.n} (64 clusters, std 300 um, 10 mm cube, "
                        f"Poisson(2) vacancies 0..8, 20% inhibitory)",
@@ -379,7 +397,7 @@ def run_ours(args):
     achieved = flops / (res["kernel_ms"] / 1000.0) / 1e12 if res["kernel_ms"] > 0 else 0.0
     roof = {"bound": "alu", "kernel": "bh_search_kernel", "achieved": achieved,
             "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-            "traffic": None,
+            "traffic": search_traffic(),
             "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop/FMA x "
                            f"{clock_mhz:.0f} MHz (FP32 pipe; MEASURED_PEAKS.json has only HBM and "
                            f"bf16 peaks, {src})",
