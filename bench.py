@@ -15,6 +15,13 @@ time (device time, CUDA events); L2 is flushed between steps.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload.
+
+--workload batch measures the batched form instead: 256 independent networks
+(log-uniform 10^3 .. 10^6 neurons, about 3.7e7 in total, constant density,
+per-network sigma in [500, 1000] um, theta = 0.3). One step = the batched octree
+build of all networks + one connectivity update of all of them (one search
+launch) + full deletion, captured once in a CUDA graph and replayed; the search
+kernel's walk width is chosen by the autotuner before capture.
 """
 from __future__ import annotations
 
@@ -50,6 +57,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--group", type=int, default=0,
                     help="source neurons per octree walk in the search kernel (0 = default)")
+    ap.add_argument("--workload", choices=["clusters", "batch"], default="clusters")
+    ap.add_argument("--networks", type=int, default=256)
     return ap.parse_args()
 
 
@@ -428,10 +437,241 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------- batched form
+BATCH_METRIC = ("neuron-searches/sec per connectivity update, batched form: 256 networks of "
+                "10^3..10^6 neurons in one launch; % of GB300 roofline")
+
+
+def batch_workload(networks):
+    from paper_2509_26193_gb300 import workloads
+    return workloads.network_batch(networks=networks, seed=4)
+
+
+def batch_config(b, extra=None):
+    cfg = {"workload": f"network_batch: {b.num_networks} networks, sizes log-uniform "
+                       f"{b.params['n_range']}, n={b.n}, uniform at 4096 neurons/mm^3, "
+                       f"Poisson(2) vacancies 0..8, sigma U[500, 1000] um per network, "
+                       f"20% inhibitory",
+           "n": b.n, "networks": b.num_networks, "theta": b.theta,
+           "step": "batched build + 1 update (all networks, one search launch) + full "
+                   "deletion, one CUDA graph replay",
+           "l2": f"inputs larger than L2 ({12 * b.n / 1e6:.0f} MB of positions) and 256 MB "
+                 f"flush between steps"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+class BatchRunner:
+    def __init__(self, b, device):
+        import torch
+        from paper_2509_26193_gb300 import build, relearn as R
+        build.build()
+        self.torch, self.R, self.b = torch, R, b
+        d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        self.x, self.y, self.z = d(b.x), d(b.y), d(b.z)
+        self.vac_ax0, self.vac_de0 = d(b.vac_ax), d(b.vac_de)
+        self.vac_ax, self.vac_de = self.vac_ax0.clone(), self.vac_de0.clone()
+        self.type, self.sigma = d(b.type), d(b.sigma)
+        self.retract = torch.full((b.n,), 1 << 20, dtype=torch.int32, device=device)
+        q = int(b.vac_ax.sum())
+        cap = int(min(q, int(b.vac_de.sum()))) + 1024
+        self.ctx = R.relearn_create_batched(b.n, cap, b.num_networks, q + 1024,
+                                            device=device.index)
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        self.h = {k: pin(getattr(b, k)) for k in ("x", "y", "z", "vac_ax", "vac_de", "type")}
+        self.h_out = torch.empty(b.n, dtype=torch.int32).pin_memory()
+        self.group = 0
+        self.graph = None
+
+    def step(self, flags=0, group=None):
+        R, b = self.R, self.b
+        self.vac_ax.copy_(self.vac_ax0)
+        self.vac_de.copy_(self.vac_de0)
+        R.relearn_build_octree_batch(self.ctx, b.offsets, self.x, self.y, self.z)
+        p = R.params(0.0, b.theta, b.seed, 1, flags, self.group if group is None else group,
+                     net_sigma=self.sigma)
+        R.relearn_update_connectivity(self.ctx, p, self.vac_ax, self.vac_de, self.type)
+        p = R.params(0.0, b.theta, b.seed, 999, 0, 0, net_sigma=self.sigma)
+        R.relearn_delete_synapses(self.ctx, p, self.retract, self.retract, self.vac_ax,
+                                  self.vac_de)
+
+    def trial(self, group):
+        """One direct (uncaptured) step with the search kernel timed: kernel ms."""
+        self.R.relearn_collect_search_times(self.ctx)
+        self.step(self.R.FLAG_TIMING, group)
+        self.torch.cuda.synchronize()
+        ms, n = self.R.relearn_collect_search_times(self.ctx)
+        return ms / max(n, 1)
+
+    def capture(self):
+        torch = self.torch
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step()
+        torch.cuda.synchronize()
+
+    def counters(self):
+        s = self.R.relearn_get_last_stats(self.ctx)
+        return s["searches_total"], s["evals_total"]
+
+    def timed(self, steps, e2e=False):
+        torch = self.torch
+        st = torch.cuda.current_stream()
+        total = 0.0
+        q0, e0 = self.counters()
+        l0 = self.R.relearn_launch_count()
+        for _ in range(steps):
+            self.flush.zero_()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            c = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            if e2e:
+                for k in ("x", "y", "z", "type"):
+                    getattr(self, k).copy_(self.h[k], non_blocking=True)
+                self.vac_ax0.copy_(self.h["vac_ax"], non_blocking=True)
+                self.vac_de0.copy_(self.h["vac_de"], non_blocking=True)
+            self.graph.replay()
+            if e2e:
+                self.h_out.copy_(self.vac_ax, non_blocking=True)
+            c.record(st)
+            torch.cuda.synchronize()
+            total += a.elapsed_time(c)
+        q1, e1 = self.counters()
+        return {"ms": total, "searches": q1 - q0, "evals": e1 - e0,
+                "launches_host": self.R.relearn_launch_count() - l0}
+
+    def h2d_bytes(self):
+        return 21 * self.b.n
+
+    def d2h_bytes(self):
+        return 4 * self.b.n
+
+
+def batch_cpu_baseline(b, sample=1 << 15):
+    """The FP64 oracle on the host cores, on the batch's largest network: its tree build,
+    bottom-up update and a random sample of its searches, scaled to all of its searches."""
+    import oracle
+    oracle.build()
+    threads = (os.cpu_count() or 1) if oracle.openmp_available() else 1
+    k = int(np.argmax(np.diff(b.offsets)))
+    net = b.network(k)
+    lo = int(b.offsets[k])
+    t0 = time.perf_counter()
+    t = oracle.Tree(net.x, net.y, net.z, id_base=lo)
+    t.reduce(net.vac_de)
+    t1 = time.perf_counter()
+    qi, qe = oracle.queries(net.vac_ax)
+    sel = np.sort(np.random.default_rng(0).choice(len(qi), min(sample, len(qi)), replace=False))
+    t2 = time.perf_counter()
+    t.search_batch(net.sigma, b.theta, b.seed, 1, qi[sel], qe[sel], threads=threads)
+    t3 = time.perf_counter()
+    est = (t1 - t0) + (t3 - t2) * len(qi) / len(sel)
+    return {"value": len(qi) / est, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"largest network of the batch (n={net.n}): octree build + bottom-up "
+                      f"update ({t1 - t0:.2f} s) + {len(sel)} of its {len(qi)} searches "
+                      f"({t3 - t2:.2f} s), scaled to all of its searches"}
+
+
+def run_batch(args):
+    import torch
+    from paper_2509_26193_gb300 import autotune
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local if ws > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(device)
+    b = batch_workload(args.networks)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = batch_cpu_baseline(b)
+    run = BatchRunner(b, device)
+    run.step()
+    torch.cuda.synchronize()
+    if args.group:
+        best, table = args.group, {}
+    else:
+        best, table = autotune.tune(run.trial)
+    run.group = best
+    # launches of one step, counted on direct calls (a graph replay makes the same ones)
+    l0 = run.R.relearn_launch_count()
+    run.step()
+    torch.cuda.synchronize()
+    launches_per_step = run.R.relearn_launch_count() - l0
+    # search kernel time of one step with the chosen width (for the roofline)
+    ks = [run.trial(best) for _ in range(3)]
+    q0, e0 = run.counters()
+    run.step()
+    torch.cuda.synchronize()
+    q1, e1 = run.counters()
+    run.capture()
+    for _ in range(max(args.warmup, 3)):
+        run.graph.replay()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = ClockSampler(device.index)
+    clocks.start()
+    res = run.timed(args.steps)
+    clk = clocks.stop()
+    units, secs = aggregate(res["searches"], res["ms"] / 1000.0, ws, device)
+    e2e = None
+    if not args.no_e2e:
+        r2 = run.timed(args.steps, e2e=True)
+        u2, s2 = aggregate(r2["searches"], r2["ms"] / 1000.0, ws, device)
+        e2e = {"value": u2 / s2, "unit": UNIT, "h2d_bytes_per_step": run.h2d_bytes(),
+               "d2h_bytes_per_step": run.d2h_bytes()}
+    if ws > 1:
+        dist.barrier()
+        if rank != 0:
+            dist.destroy_process_group()
+            return
+    k_ms = min(ks)
+    evals = e1 - e0
+    peak_tflops = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = FLOPS_PER_EVAL * evals / (k_ms / 1000.0) / 1e12
+    roof = {"bound": "alu", "kernel": "bh_search_kernel", "achieved": achieved,
+            "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+            "traffic": None,
+            "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop/FMA x "
+                           f"{SM_MAX_MHZ:.0f} MHz (FP32 pipe)",
+            "work": f"{FLOPS_PER_EVAL} flop per node evaluation x {evals} evaluations in one "
+                    f"launch (one step, timed uncaptured with CUDA events)",
+            "kernel_ms_per_launch": k_ms,
+            "kernel_share_of_step": k_ms / (res["ms"] / args.steps)}
+    line = {"metric": BATCH_METRIC, "value": units / secs, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": batch_config(b, {
+                "parallelism": "replicas" if ws > 1 else "single GPU",
+                "searches_per_step": res["searches"] / args.steps,
+                "evals_per_search": evals / max(q1 - q0, 1),
+                "search_group": best, "autotune_ms": table,
+                "graph": "build + update + deletion captured once, replayed per step"}),
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "roofline": roof, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -59,7 +59,12 @@ typedef struct relearn_ctx relearn_ctx;
  *             0 = chosen per warp from how close its sources are (default);
  *             1000 + 100 * d32 + d8 (d32, d8 = 0..10) = chosen per warp: 32 together when
  *             they share a cell of depth >= d32, else 8 together when they share a cell of
- *             depth >= d8, else one by one. */
+ *             depth >= d8, else one by one.
+ *   net_sigma, net_theta  device float[num_networks] or NULL (updates only): per-network
+ *             sigma and theta of a batched build (relearn_build_octree_batch), replacing the
+ *             scalars for network b. Values are checked on the device: a sigma that is not
+ *             in (0, 3e38) or a theta not in [0, 3e38) sets INVALID_ARG in the device status
+ *             and the update applies nothing. */
 typedef struct {
     float sigma;
     float theta;
@@ -67,6 +72,8 @@ typedef struct {
     uint64_t step;
     uint32_t flags;
     uint32_t search_group;
+    const float *net_sigma;
+    const float *net_theta;
 } relearn_params;
 
 /* Record per-search diagnostics (root-frontier ln S, node evaluations, restarts),
@@ -104,6 +111,15 @@ typedef struct {
 relearn_status relearn_create(relearn_ctx **out, int device, int64_t max_neurons,
                               int64_t max_synapses, int64_t max_searches);
 
+/* As relearn_create, for batched builds of up to max_networks independent networks
+ * (relearn_build_octree_batch); max_networks in 1 .. RELEARN_MAX_NETWORKS. The batched
+ * form has no counterpart in the paper, which updates one network: it packs many small
+ * networks into one build and one search launch so the GPU is filled. */
+#define RELEARN_MAX_NETWORKS 65536
+relearn_status relearn_create_batched(relearn_ctx **out, int device, int64_t max_neurons,
+                                      int64_t max_synapses, int64_t max_searches,
+                                      int32_t max_networks);
+
 /* Free the context and all of its device memory (synchronises the device). NULL is ok. */
 relearn_status relearn_destroy(relearn_ctx *ctx);
 
@@ -123,6 +139,24 @@ relearn_status relearn_destroy(relearn_ctx *ctx);
 relearn_status relearn_build_octree(relearn_ctx *ctx, int64_t n, const float *x, const float *y,
                                     const float *z, const int32_t *vac_de, const float *box_lo3,
                                     const float *box_hi3, void *stream);
+
+/* Build one octree per network for num_networks independent networks in one pass (no
+ * counterpart in the paper; each network is the single network of Sec. III-B).
+ *   offsets   host int64[num_networks + 1]: network b holds neuron ids offsets[b] ..
+ *             offsets[b + 1] - 1; offsets[0] = 0, strictly increasing (no empty network),
+ *             offsets[num_networks] = n <= max_neurons. The offsets are staged in pinned
+ *             memory owned by the context; a build captured into a CUDA graph reads the
+ *             offsets of the latest build call when the graph runs.
+ *   x, y, z, vac_de  as relearn_build_octree, over all n neurons.
+ * Each network's domain is the bounding box of its own positions. Every later call works
+ * on all networks at once: an update searches each neuron's own network only (a network's
+ * tree is its own subtree, so no synapse crosses networks), with per-network sigma/theta
+ * from relearn_params.net_sigma/net_theta; Philox counters use the global neuron ids.
+ * Errors: INVALID_ARG for bad offsets, num_networks outside 1 .. the context's
+ * max_networks, NULL positions. */
+relearn_status relearn_build_octree_batch(relearn_ctx *ctx, int32_t num_networks,
+                                          const int64_t *offsets, const float *x, const float *y,
+                                          const float *z, const int32_t *vac_de, void *stream);
 
 /* One connectivity update (Sec. III-A "Update of synapses", formation sub-phase, with the
  * Barnes-Hut search of Sec. III-B):

@@ -76,6 +76,7 @@ def lib():
                 "orc_morton": (None, [_I64, _P, _P, _P, _P, _P, _P, _P, _P]),
                 "orc_tree_build": (_P, [_I64, _P, _P, _P, _P, _P]),
                 "orc_tree_free": (None, [_P]),
+                "orc_tree_set_id_base": (None, [_P, _I64]),
                 "orc_tree_num_nodes": (_I64, [_P]),
                 "orc_tree_box": (None, [_P, _P, _P]),
                 "orc_tree_canonical_order": (None, [_P, _P]),
@@ -137,13 +138,18 @@ def morton(x, y, z, box_lo=None, box_hi=None):
 class Tree:
     """Pointer octree over the positions (Sec. III-B "Spatial octree")."""
 
-    def __init__(self, x, y, z, box_lo=None, box_hi=None):
+    def __init__(self, x, y, z, box_lo=None, box_hi=None, id_base=0):
+        """id_base: global id of neuron 0 when the tree holds one network of a batch
+        (the search draws are keyed by global ids); results stay local ids."""
         self._x, self._y, self._z = (_c(a, np.float32) for a in (x, y, z))
         self.n = self._x.shape[0]
         bl = None if box_lo is None else _c(box_lo, np.float32)
         bh = None if box_hi is None else _c(box_hi, np.float32)
         self._h = lib().orc_tree_build(self.n, _p(self._x), _p(self._y), _p(self._z),
                                        _p(bl), _p(bh))
+        self.id_base = int(id_base)
+        if self.id_base:
+            lib().orc_tree_set_id_base(self._h, self.id_base)
 
     def close(self):
         if self._h:
@@ -315,5 +321,38 @@ def update_connectivity(tree: Tree, vac_ax, vac_de, type_, sigma, theta, seed, s
     qi, qe = queries(vac_ax)
     tgt, diag = tree.search_batch(sigma, theta, seed, step, qi, qe, threads=threads)
     acc = accept(tree.n, qi, qe, tgt, vac_de, seed, step)
+    formed = apply(qi, tgt, acc, type_, vac_ax, vac_de, syn)
+    return {"src": qi, "elem": qe, "tgt": tgt, "accept": acc, "diag": diag, "formed": formed}
+
+
+def update_connectivity_batch(trees, offsets, vac_ax, vac_de, type_, sigmas, theta, seed, step,
+                              syn: Synapses, threads=1):
+    """Batched form: independent networks, network b = global ids offsets[b] ..
+    offsets[b + 1] - 1 with its own tree (built with id_base = offsets[b]) and sigma.
+    Each network searches only its own tree (Sec. III-B per network); the requests of
+    all networks then go through one acceptance and one apply over the global ids,
+    which equals doing them network by network since no request crosses networks.
+
+    Same return dict as update_connectivity, requests in global canonical order.
+    """
+    offsets = np.asarray(offsets, np.int64)
+    qi_all, qe_all, tgt_all, diag_all = [], [], [], []
+    for b, tree in enumerate(trees):
+        lo, hi = int(offsets[b]), int(offsets[b + 1])
+        assert tree.n == hi - lo and tree.id_base == lo
+        tree.reduce(vac_de[lo:hi])
+        qi, qe = queries(vac_ax[lo:hi])
+        tgt, diag = tree.search_batch(float(sigmas[b]), theta, seed, step, qi, qe,
+                                      threads=threads)
+        qi_all.append(qi.astype(np.int64) + lo)
+        qe_all.append(qe)
+        tgt_all.append(np.where(tgt >= 0, tgt.astype(np.int64) + lo, -1))
+        diag_all.append(diag)
+    qi = np.concatenate(qi_all).astype(np.int32)
+    qe = np.concatenate(qe_all).astype(np.int32)
+    tgt = np.concatenate(tgt_all).astype(np.int32)
+    diag = np.concatenate(diag_all)
+    n = int(offsets[-1])
+    acc = accept(n, qi, qe, tgt, vac_de, seed, step)
     formed = apply(qi, tgt, acc, type_, vac_ax, vac_de, syn)
     return {"src": qi, "elem": qe, "tgt": tgt, "accept": acc, "diag": diag, "formed": formed}

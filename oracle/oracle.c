@@ -196,6 +196,7 @@ typedef struct {
 
 typedef struct {
     int64_t n;
+    int64_t id_base;                /* global id of neuron 0 (one network of a batch) */
     float lo[3], hi[3];
     double len2[ORC_MAX_DEPTH + 2]; /* (cell length)^2 per depth, R2 */
     double *px, *py, *pz;           /* positions as FP64 (exact copies of FP32 input) */
@@ -333,6 +334,10 @@ void *orc_tree_build(int64_t n, const float *x, const float *y, const float *z,
     free(scratch);
     return T;
 }
+
+/* Batched form: the tree holds one network whose neurons have global ids
+ * id_base .. id_base + n - 1; the search draws are keyed by the global id. */
+void orc_tree_set_id_base(void *t, int64_t id_base) { ((OTree *)t)->id_base = id_base; }
 
 void orc_tree_free(void *t)
 {
@@ -582,8 +587,8 @@ int32_t orc_search(void *t, double sigma, double theta, uint64_t seed, uint64_t 
             free(a);
             break;
         }
-        uint32_t w = philox_x((uint32_t)i, (uint32_t)step, ((uint32_t)e << 8) | (uint32_t)ns->depth,
-                              0u, seed);
+        uint32_t w = philox_x((uint32_t)(T->id_base + i), (uint32_t)step,
+                              ((uint32_t)e << 8) | (uint32_t)ns->depth, 0u, seed);
         double u = (double)w * (1.0 / 4294967296.0);
         double target = u * S;
         double C = 0.0;

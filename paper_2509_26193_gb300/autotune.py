@@ -1,0 +1,33 @@
+"""Autotuner of the search kernel's launch-time knob.
+
+The search kernel walks the octree with groups of source neurons (``search_group``
+in relearn_params): 32 or 8 neurons that are close in Morton order share one walk,
+or every lane walks alone; the default picks the width per warp from the Morton
+spread of the warp's sources, with two depth thresholds. The best thresholds
+depend on the workload (cluster sizes, density, sigma relative to the domain).
+Results never depend on the choice, only the time does, so the tuner simply
+times each candidate on the caller's own update and keeps the fastest.
+
+The tuner runs trials through a caller-supplied function that performs one
+update with the given ``search_group`` and returns the search kernel's device
+milliseconds (e.g. from ``relearn_collect_search_times`` after an update with
+``FLAG_TIMING``); the caller restores its state between trials.
+"""
+from __future__ import annotations
+
+from typing import Callable, Dict, Iterable, Tuple
+
+# 0 = the library's default thresholds; 1 / 8 / 32 = one fixed width for every
+# warp; 1000 + 100 * d32 + d8 = per-warp choice with thresholds d32 and d8.
+DEFAULT_CANDIDATES = (0, 1, 8, 32, 1302, 1303, 1402, 1403, 1503, 1504, 1604)
+
+
+def tune(trial: Callable[[int], float], candidates: Iterable[int] = DEFAULT_CANDIDATES,
+         repeats: int = 2) -> Tuple[int, Dict[int, float]]:
+    """Time every candidate ``repeats`` times (the minimum counts) and return
+    (best candidate, {candidate: ms})."""
+    table: Dict[int, float] = {}
+    for c in candidates:
+        table[int(c)] = min(float(trial(int(c))) for _ in range(max(repeats, 1)))
+    best = min(table, key=table.get)
+    return best, table

@@ -71,6 +71,8 @@ void free_all(relearn_ctx *c)
     void **ptrs[] = {
         (void **)&c->d_status,   (void **)&c->d_i64,        (void **)&c->d_i32,
         (void **)&c->d_geom,     (void **)&c->d_sc,         (void **)&c->d_codes,
+        (void **)&c->d_off,      (void **)&c->d_ord,        (void **)&c->d_root,
+        (void **)&c->d_net,      (void **)&c->d_nkey,       (void **)&c->d_nkey_alt,
         (void **)&c->d_codes_alt, (void **)&c->d_perm,      (void **)&c->d_perm_alt,
         (void **)&c->d_pos,      (void **)&c->d_posq,       (void **)&c->d_mask,       (void **)&c->d_base,
         (void **)&c->d_nodes,    (void **)&c->d_parent,     (void **)&c->d_nsize,
@@ -94,6 +96,10 @@ void free_all(relearn_ctx *c)
         *p = nullptr;
     }
     c->sort.scan.block_sums = nullptr;
+    if (c->h_off) cudaFreeHost(c->h_off);
+    c->h_off = nullptr;
+    if (c->off_ev) cudaEventDestroy(c->off_ev);
+    c->off_ev = nullptr;
     for (cudaEvent_t &ev : c->ev)
         if (ev) {
             cudaEventDestroy(ev);
@@ -109,8 +115,9 @@ void free_all(relearn_ctx *c)
 
 bool params_ok(const relearn_params *p)
 {
-    return p && p->sigma > 0.0f && p->sigma < 3.0e38f && p->theta >= 0.0f &&
-           p->theta < 3.0e38f && p->step <= 0xffffffffull &&
+    return p && (p->net_sigma || (p->sigma > 0.0f && p->sigma < 3.0e38f)) &&
+           (p->net_theta || (p->theta >= 0.0f && p->theta < 3.0e38f)) &&
+           p->step <= 0xffffffffull &&
            (p->search_group == 0 || p->search_group == 1 || p->search_group == 8 ||
             p->search_group == 16 || p->search_group == 32 ||
             (p->search_group >= 1000 && p->search_group <= 2010 &&
@@ -146,11 +153,19 @@ extern "C" {
 relearn_status relearn_create(relearn_ctx **out, int device, int64_t max_neurons,
                               int64_t max_synapses, int64_t max_searches)
 {
+    return relearn_create_batched(out, device, max_neurons, max_synapses, max_searches, 1);
+}
+
+relearn_status relearn_create_batched(relearn_ctx **out, int device, int64_t max_neurons,
+                                      int64_t max_synapses, int64_t max_searches,
+                                      int32_t max_networks)
+{
     if (!out) return RELEARN_ERR_INVALID_ARG;
     *out = nullptr;
     if (max_neurons < 1 || max_neurons > (int64_t)0x3fffffff || max_synapses < 1 ||
         max_synapses > (int64_t)0x7ffffff0 || max_searches < 0 ||
-        max_searches > (int64_t)0x7ffffff0)
+        max_searches > (int64_t)0x7ffffff0 || max_networks < 1 ||
+        max_networks > RELEARN_MAX_NETWORKS || max_networks > max_neurons)
         return RELEARN_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
@@ -163,6 +178,7 @@ relearn_status relearn_create(relearn_ctx **out, int device, int64_t max_neurons
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (c->num_sms < 1) c->num_sms = 1;
     c->max_neurons = max_neurons;
+    c->max_nets = max_networks;
     c->max_synapses = max_synapses;
     c->max_searches = max_searches ? max_searches : std::min<int64_t>(8 * max_neurons, 0x7ffffff0);
     c->max_nodes = 2 * max_neurons + 1;
@@ -174,8 +190,17 @@ relearn_status relearn_create(relearn_ctx **out, int device, int64_t max_neurons
     A(d_status, 1);
     A(d_i64, 16);
     A(d_i32, 32);
-    A(d_geom, 1);
-    A(d_sc, 1);
+    const int64_t NB = max_networks;
+    A(d_geom, NB);
+    A(d_sc, NB);
+    A(d_off, NB + 1);
+    A(d_ord, 6 * NB);
+    A(d_root, NB);
+    if (NB > 1) {
+        A(d_net, N);
+        A(d_nkey, N);
+        A(d_nkey_alt, N);
+    }
     A(d_codes, N);
     A(d_codes_alt, N);
     A(d_perm, N);
@@ -243,6 +268,8 @@ relearn_status relearn_create(relearn_ctx **out, int device, int64_t max_neurons
             for (cudaEvent_t &ev : pair)
                 if (e == cudaSuccess) e = cudaEventCreate(&ev);
     }
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_off, (NB + 1) * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->off_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->d_i64, 0, 16 * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMemset(c->d_i32, 0, 32 * sizeof(int32_t));
@@ -288,7 +315,55 @@ relearn_status relearn_build_octree(relearn_ctx *c, int64_t n, const float *x, c
     c->last_stream = st;
     const bool reset_store = !c->built || n != c->n;
     c->n = n;
-    CK(octree_build(c, n, x, y, z, box_lo3, box_hi3, st), "octree build");
+    c->num_nets = 1;
+    CK(octree_build(c, n, 1, x, y, z, box_lo3, box_hi3, st), "octree build");
+    if (vac_de) CK(octree_reduce(c, vac_de, st), "octree reduce");
+    if (reset_store) {
+        CK(cudaMemsetAsync(c->d_i32 + I32_NSYN, 0, sizeof(int32_t), st), "store reset");
+        CK(cudaMemsetAsync(c->d_i64 + I64_NSYN, 0, sizeof(int64_t), st), "store reset");
+        CK(rebuild_views(c, st), "views");
+    }
+    c->built = true;
+    c->diag_valid = false;
+    return RELEARN_OK;
+}
+
+relearn_status relearn_build_octree_batch(relearn_ctx *c, int32_t num_networks,
+                                          const int64_t *offsets, const float *x, const float *y,
+                                          const float *z, const int32_t *vac_de, void *stream)
+{
+    if (!c) return RELEARN_ERR_INVALID_ARG;
+    if (num_networks < 1 || num_networks > c->max_nets)
+        return fail(c, RELEARN_ERR_INVALID_ARG, "build_octree_batch: num_networks out of range");
+    if (!offsets || !x || !y || !z)
+        return fail(c, RELEARN_ERR_INVALID_ARG, "build_octree_batch: NULL argument");
+    if (offsets[0] != 0)
+        return fail(c, RELEARN_ERR_INVALID_ARG, "build_octree_batch: offsets[0] != 0");
+    for (int32_t b = 0; b < num_networks; ++b)
+        if (!(offsets[b + 1] > offsets[b]))
+            return fail(c, RELEARN_ERR_INVALID_ARG,
+                        "build_octree_batch: offsets not strictly increasing");
+    const int64_t n = offsets[num_networks];
+    if (n > c->max_neurons)
+        return fail(c, RELEARN_ERR_INVALID_ARG, "build_octree_batch: n > max_neurons");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(c, RELEARN_ERR_CUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    // The staging buffer may still feed the previous build's copy (not while capturing:
+    // then nothing has run yet).
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs), "capture status");
+    if (cs == cudaStreamCaptureStatusNone) CK(cudaEventSynchronize(c->off_ev), "staging wait");
+    memcpy(c->h_off, offsets, (size_t)(num_networks + 1) * sizeof(int64_t));
+    CK(cudaMemcpyAsync(c->d_off, c->h_off, (num_networks + 1) * sizeof(int64_t),
+                       cudaMemcpyHostToDevice, st),
+       "offsets");
+    CK(cudaEventRecord(c->off_ev, st), "event");
+    const bool reset_store = !c->built || n != c->n;
+    c->n = n;
+    c->num_nets = num_networks;
+    CK(octree_build(c, n, num_networks, x, y, z, nullptr, nullptr, st), "octree build");
     if (vac_de) CK(octree_reduce(c, vac_de, st), "octree reduce");
     if (reset_store) {
         CK(cudaMemsetAsync(c->d_i32 + I32_NSYN, 0, sizeof(int32_t), st), "store reset");

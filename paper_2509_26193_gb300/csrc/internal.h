@@ -45,6 +45,8 @@ struct relearn_ctx {
     int device = 0;
     int num_sms = 0;
     int64_t max_neurons = 0, max_synapses = 0, max_searches = 0, max_nodes = 0;
+    int32_t max_nets = 1; // networks one build may hold
+    int32_t num_nets = 1; // networks in the current tree
     cudaStream_t last_stream = nullptr;
     bool built = false;
     int64_t n = 0; // neurons in the current tree
@@ -55,8 +57,17 @@ struct relearn_ctx {
     int32_t *d_status = nullptr;   // first device error code
     int64_t *d_i64 = nullptr;      // [16] counters and totals
     int32_t *d_i32 = nullptr;      // [16] element counts used as kernel bounds
-    rl::Geom *d_geom = nullptr;
-    rl::SearchConst *d_sc = nullptr;
+    rl::Geom *d_geom = nullptr;      // [max_nets]
+    rl::SearchConst *d_sc = nullptr; // [max_nets]
+
+    // ---- networks: b holds neurons off[b] .. off[b + 1] - 1 (ids and Morton positions)
+    int64_t *d_off = nullptr;     // [max_nets + 1]
+    int64_t *h_off = nullptr;     // [max_nets + 1] pinned staging of the offsets
+    cudaEvent_t off_ev = nullptr; // the last copy out of h_off
+    uint32_t *d_ord = nullptr;    // [6 * max_nets] bounding boxes (ordered-int min, max)
+    int32_t *d_root = nullptr;    // [max_nets] root node of each network
+    int32_t *d_net = nullptr;     // [n] network of each Morton position (max_nets > 1)
+    uint64_t *d_nkey = nullptr, *d_nkey_alt = nullptr; // [n] (network, code) sort keys
 
     // ---- tree (per build)
     uint32_t *d_codes = nullptr, *d_codes_alt = nullptr; // [n]
@@ -144,7 +155,7 @@ cudaError_t radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, int32_t *vals, in
 int64_t sort_blocks_needed(int64_t max_n);
 
 // octree.cu -----------------------------------------------------------------
-cudaError_t octree_build(relearn_ctx *c, int64_t n, const float *x, const float *y,
+cudaError_t octree_build(relearn_ctx *c, int64_t n, int32_t B, const float *x, const float *y,
                          const float *z, const float *box_lo, const float *box_hi,
                          cudaStream_t st);
 cudaError_t octree_reduce(relearn_ctx *c, const int32_t *vac_de, cudaStream_t st);

@@ -31,52 +31,80 @@ __device__ __forceinline__ float unordered(uint32_t u)
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
-// d_ord[0..2] = min (ordered), d_ord[3..5] = max (ordered); NaN positions are skipped.
-__global__ void bbox_kernel(const float *__restrict__ x, const float *__restrict__ y,
-                            const float *__restrict__ z, int64_t n, uint32_t *d_ord)
+// Network of neuron (or Morton position) i: the b with off[b] <= i < off[b + 1].
+__device__ __forceinline__ int32_t net_of(const int64_t *__restrict__ off, int32_t B, int64_t i)
 {
-    uint32_t mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0u, 0u, 0u};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        float p[3] = {x[i], y[i], z[i]};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (p[a] != p[a]) continue;
-            uint32_t o = ordered(p[a]);
-            mn[a] = min(mn[a], o);
-            mx[a] = max(mx[a], o);
-        }
+    int32_t lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
     }
+    return lo;
+}
+
+// Network of Morton position s; one network keeps no per-position array.
+__device__ __forceinline__ int32_t net_at(const int32_t *__restrict__ net, int64_t s)
+{
+    return net ? net[s] : 0;
+}
+
+// Per network b: d_ord[6b .. 6b+2] = min (ordered), d_ord[6b+3 .. 6b+5] = max; NaN
+// coordinates are skipped. A warp whose 32 elements share a network reduces them
+// before its atomics; elements at network boundaries go one by one.
+__global__ void bbox_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                            const float *__restrict__ z, int64_t n,
+                            const int64_t *__restrict__ off, int32_t B, uint32_t *d_ord)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < n;
+         w0 += wstride) {
+        const int64_t i = w0 + lane;
+        const bool ok = i < n;
+        const int32_t b = ok ? (B == 1 ? 0 : net_of(off, B, i)) : -1;
+        uint32_t mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0u, 0u, 0u};
+        if (ok) {
+            const float p[3] = {x[i], y[i], z[i]};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        for (int off = 16; off; off >>= 1) {
-            mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], off));
-            mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], off));
+            for (int a = 0; a < 3; ++a)
+                if (p[a] == p[a]) mn[a] = mx[a] = ordered(p[a]);
         }
-    }
-    __shared__ uint32_t smn[3][32], smx[3][32];
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if ((threadIdx.x & 31) == 0)
-        for (int a = 0; a < 3; ++a) {
-            smn[a][warp] = mn[a];
-            smx[a][warp] = mx[a];
+        const int32_t b0 = __shfl_sync(0xffffffffu, b, 0);
+        const int32_t b31 = __shfl_sync(0xffffffffu, ok ? b : b0, 31);
+        if (b0 == b31) { // every valid lane is in network b0
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                for (int o = 16; o; o >>= 1) {
+                    mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+                    mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+                }
+            if (lane == 0)
+                for (int a = 0; a < 3; ++a) {
+                    atomicMin(&d_ord[6 * b0 + a], mn[a]);
+                    atomicMax(&d_ord[6 * b0 + 3 + a], mx[a]);
+                }
+        } else if (ok) {
+            for (int a = 0; a < 3; ++a) {
+                atomicMin(&d_ord[6 * b + a], mn[a]);
+                atomicMax(&d_ord[6 * b + 3 + a], mx[a]);
+            }
         }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-        const int a = threadIdx.x;
-        uint32_t bmn = 0xffffffffu, bmx = 0u;
-        for (int w = 0; w < nw; ++w) {
-            bmn = min(bmn, smn[a][w]);
-            bmx = max(bmx, smx[a][w]);
-        }
-        atomicMin(&d_ord[a], bmn);
-        atomicMax(&d_ord[3 + a], bmx);
     }
 }
 
-__global__ void bbox_init_kernel(uint32_t *d_ord)
+// Also writes the offsets {0, n} of a single network when off_one is given.
+__global__ void bbox_init_kernel(uint32_t *d_ord, int32_t B, int64_t *off_one, int64_t n)
 {
-    if (threadIdx.x < 6) d_ord[threadIdx.x] = threadIdx.x < 3 ? 0xffffffffu : 0u;
+    if (off_one && blockIdx.x == 0 && threadIdx.x == 0) {
+        off_one[0] = 0;
+        off_one[1] = n;
+    }
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 6 * (int64_t)B;
+         k += (int64_t)gridDim.x * blockDim.x)
+        d_ord[k] = (k % 6) < 3 ? 0xffffffffu : 0u;
 }
 
 struct Box {
@@ -89,8 +117,12 @@ struct Box {
 // The fixed-point frame of the bottom-up sums covers the box and every position:
 // origin = min(box lo, position min), 2^k chosen so that the largest span is
 // below 2^30 units.
-__global__ void geom_kernel(const uint32_t *d_ord, Box box, Geom *g)
+__global__ void geom_kernel(const uint32_t *d_ord_all, Box box, Geom *g_all, int32_t B)
 {
+    const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const uint32_t *d_ord = d_ord_all + 6 * b;
+    Geom *g = g_all + b;
     float lo[3], hi[3], blo[3], bhi[3];
     for (int a = 0; a < 3; ++a) {
         const bool any = d_ord[a] != 0xffffffffu; // else every coordinate is NaN
@@ -121,11 +153,13 @@ __global__ void geom_kernel(const uint32_t *d_ord, Box box, Geom *g)
 }
 
 __global__ void fixed_pos_kernel(const float4 *__restrict__ pos, int64_t n,
-                                 const Geom *__restrict__ g, int4 *__restrict__ posq)
+                                 const int32_t *__restrict__ net, const Geom *__restrict__ g_all,
+                                 int4 *__restrict__ posq)
 {
-    const double ox = g->fx_lo[0], oy = g->fx_lo[1], oz = g->fx_lo[2], sc = g->fx_scale;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (int64_t)gridDim.x * blockDim.x) {
+        const Geom *g = g_all + net_at(net, s);
+        const double ox = g->fx_lo[0], oy = g->fx_lo[1], oz = g->fx_lo[2], sc = g->fx_scale;
         const float4 p = pos[s];
         // NaN or out-of-range coordinates become 0 (the cast is defined as saturating)
         posq[s] = make_int4(__double2int_rn(((double)p.x - ox) * sc),
@@ -152,20 +186,41 @@ __device__ __forceinline__ uint32_t quantise(float x, float lo, float inv)
     return __float2uint_rz(t);
 }
 
+// 30-bit Morton code of neuron i in its network's domain. One network: codes32;
+// several: keys64 = (network << 30) | code, so one sort orders networks, then space.
 __global__ void morton_kernel(const float *__restrict__ x, const float *__restrict__ y,
-                              const float *__restrict__ z, int64_t n, const Geom *__restrict__ g,
-                              uint32_t *__restrict__ codes, int32_t *__restrict__ ids)
+                              const float *__restrict__ z, int64_t n,
+                              const int64_t *__restrict__ off, int32_t B,
+                              const Geom *__restrict__ g_all, uint32_t *__restrict__ codes32,
+                              uint64_t *__restrict__ keys64, int32_t *__restrict__ ids)
 {
-    const float lx = g->lo[0], ly = g->lo[1], lz = g->lo[2];
-    const float ix = g->inv[0], iy = g->inv[1], iz = g->inv[2];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t qx = quantise(x[i], lx, ix), qy = quantise(y[i], ly, iy),
-                 qz = quantise(z[i], lz, iz);
-        codes[i] = spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
+        const int32_t b = B == 1 ? 0 : net_of(off, B, i);
+        const Geom *g = g_all + b;
+        uint32_t qx = quantise(x[i], g->lo[0], g->inv[0]), qy = quantise(y[i], g->lo[1], g->inv[1]),
+                 qz = quantise(z[i], g->lo[2], g->inv[2]);
+        const uint32_t code = spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
+        if (B == 1)
+            codes32[i] = code;
+        else
+            keys64[i] = ((uint64_t)b << 30) | code;
         ids[i] = (int32_t)i;
     }
 }
+
+__global__ void split_keys_kernel(const uint64_t *__restrict__ keys, int64_t n,
+                                  uint32_t *__restrict__ codes, int32_t *__restrict__ net)
+{
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[s];
+        codes[s] = (uint32_t)(k & 0x3fffffffu);
+        net[s] = (int32_t)(k >> 30);
+    }
+}
+
+
 
 __global__ void gather_pos_kernel(const float *__restrict__ x, const float *__restrict__ y,
                                   const float *__restrict__ z, const int32_t *__restrict__ perm,
@@ -213,29 +268,35 @@ __device__ __forceinline__ int64_t upper_bound_prefix(const uint32_t *codes, int
     return lo;
 }
 
-// Each adjacent pair (j, j+1) that first separates two child cells of a depth-d
-// cell (d = common digits) marks that cell as a node: bit d of mask[cell start].
-__global__ void topo_pairs_kernel(const uint32_t *__restrict__ codes, int64_t n,
+// Each adjacent pair (j, j+1) of one network that first separates two child cells
+// of a depth-d cell (d = common digits) marks that cell as a node: bit d of
+// mask[cell start]. The first position of every network holds its root (bit 0).
+__global__ void topo_pairs_kernel(const uint32_t *__restrict__ codes,
+                                  const int32_t *__restrict__ net,
+                                  const int64_t *__restrict__ off, int64_t n,
                                   uint32_t *__restrict__ mask)
 {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n - 1;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t cj = codes[j];
-        int d = common_digits(cj, codes[j + 1]);
+        const int32_t b = net_at(net, j);
+        const int64_t lo = off[b];
+        if (j == lo) atomicOr(&mask[j], 1u); // the root of network b
+        if (j + 1 >= off[b + 1]) continue;    // last neuron of its network: no pair
+        const uint32_t cj = codes[j];
+        const int d = common_digits(cj, codes[j + 1]);
         int64_t L;
         if (d == kMaxDepth) {
-            if (j > 0 && codes[j - 1] == cj) continue; // not the first pair of the bucket
+            if (j > lo && codes[j - 1] == cj) continue; // not the first pair of the bucket
             L = j;
         } else {
-            int s1 = 3 * (kMaxDepth - 1 - d); // child cell (depth d + 1) prefix
-            uint32_t key = (cj >> s1) << s1;
-            int64_t Lc = lower_bound(codes, 0, j, key);
-            if (Lc > 0 && common_digits(codes[Lc - 1], codes[Lc]) >= d) continue;
+            const int s1 = 3 * (kMaxDepth - 1 - d); // child cell (depth d + 1) prefix
+            const uint32_t key = (cj >> s1) << s1;
+            const int64_t Lc = lower_bound(codes, lo, j, key);
+            if (Lc > lo && common_digits(codes[Lc - 1], codes[Lc]) >= d) continue;
             L = Lc;
         }
         atomicOr(&mask[L], 1u << d);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&mask[0], 1u); // the root
 }
 
 __global__ void topo_count_kernel(const uint32_t *__restrict__ mask, int64_t n,
@@ -249,17 +310,20 @@ __global__ void topo_count_kernel(const uint32_t *__restrict__ mask, int64_t n,
 // Parent of a node whose shallower ancestors do not start at position i: the
 // node of depth common_digits(i-1, i) that contains positions i-1 and i.
 __device__ __forceinline__ int32_t parent_across(const uint32_t *codes, const uint32_t *mask,
-                                                 const int32_t *base, int64_t i, int *pdepth)
+                                                 const int32_t *base, int64_t lo, int64_t i,
+                                                 int *pdepth)
 {
     int dp = common_digits(codes[i - 1], codes[i]);
     int sh = 3 * (kMaxDepth - dp);
     uint32_t key = dp == 0 ? 0u : ((codes[i] >> sh) << sh);
-    int64_t Lp = lower_bound(codes, 0, i, key);
+    int64_t Lp = lower_bound(codes, lo, i, key);
     *pdepth = dp;
     return base[Lp] + __popc(mask[Lp] & ((1u << dp) - 1u));
 }
 
-__global__ void topo_emit_kernel(const uint32_t *__restrict__ codes, int64_t n,
+__global__ void topo_emit_kernel(const uint32_t *__restrict__ codes,
+                                 const int32_t *__restrict__ net,
+                                 const int64_t *__restrict__ off, int64_t n,
                                  const uint32_t *__restrict__ mask,
                                  const int32_t *__restrict__ base, Node *__restrict__ nodes,
                                  int32_t *__restrict__ parent, int32_t *__restrict__ nsize,
@@ -270,18 +334,20 @@ __global__ void topo_emit_kernel(const uint32_t *__restrict__ codes, int64_t n,
         const uint32_t m = mask[i];
         const int32_t b = base[i];
         const uint32_t ci = codes[i];
+        const int32_t nb = net_at(net, i);
+        const int64_t lo = off[nb], hi = off[nb + 1];
         int rank = 0;
         for (uint32_t mm = m; mm; mm &= mm - 1) {
             int d = __ffs(mm) - 1;
             int32_t v = b + rank;
             int sh = 3 * (kMaxDepth - d);
-            int64_t R = d == 0 ? n - 1 : upper_bound_prefix(codes, i, n, ci >> sh, sh) - 1;
+            int64_t R = d == 0 ? hi - 1 : upper_bound_prefix(codes, i, hi, ci >> sh, sh) - 1;
             int32_t par = -1;
             if (rank > 0) {
                 par = v - 1;
-            } else if (i > 0) {
+            } else if (i > lo) {
                 int pd;
-                par = parent_across(codes, mask, base, i, &pd);
+                par = parent_across(codes, mask, base, lo, i, &pd);
             }
             Node nd;
             nd.g = NodeGeo{0.f, 0.f, 0.f, 0.f};
@@ -298,7 +364,7 @@ __global__ void topo_emit_kernel(const uint32_t *__restrict__ codes, int64_t n,
             par = v - 1; // the deepest node starting at i
         } else {
             int pd;
-            par = parent_across(codes, mask, base, i, &pd);
+            par = parent_across(codes, mask, base, lo, i, &pd);
         }
         Node nd;
         nd.g = NodeGeo{0.f, 0.f, 0.f, 0.f};
@@ -308,6 +374,15 @@ __global__ void topo_emit_kernel(const uint32_t *__restrict__ codes, int64_t n,
         nsize[v] = 1;
         leaf_of[i] = v;
     }
+}
+
+// The root of network b is the first node at its first Morton position; its
+// escape index is where the next network's tree starts.
+__global__ void roots_kernel(const int32_t *__restrict__ base, const int64_t *__restrict__ off,
+                             int32_t B, int32_t *__restrict__ root)
+{
+    const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) root[b] = base[off[b]];
 }
 
 // Bottom-up update as prefix sums (Sec. III-B "Division of work": an inner node
@@ -439,15 +514,17 @@ __global__ void __launch_bounds__(256)
 // Inner nodes: exact sums from the prefix, centroid rounded once to FP32.
 __global__ void reduce_nodes_kernel(Node *__restrict__ nodes, const int32_t *__restrict__ nsize,
                                     const int64_t *d_num_nodes, const L4 *__restrict__ P,
-                                    const Geom *__restrict__ g)
+                                    const int32_t *__restrict__ net,
+                                    const Geom *__restrict__ g_all)
 {
     const int64_t m = *d_num_nodes;
-    const double ox = g->fx_lo[0], oy = g->fx_lo[1], oz = g->fx_lo[2], inv = g->fx_inv;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < m;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int2 t = *reinterpret_cast<const int2 *>(&nodes[v].t);
         if (node_is_leaf((uint32_t)t.y)) continue;
         const int32_t first = nodes[v].t.neuron;
+        const Geom *g = g_all + net_at(net, first);
+        const double ox = g->fx_lo[0], oy = g->fx_lo[1], oz = g->fx_lo[2], inv = g->fx_inv;
         const L4 s = l4_sub(P[first + nsize[v]], P[first]);
         if (s.c > 0) {
             const double r = inv / (double)s.c;
@@ -472,56 +549,75 @@ inline unsigned grid_for(int64_t n, int threads, int num_sms)
 
 } // namespace
 
-cudaError_t octree_build(relearn_ctx *c, int64_t n, const float *x, const float *y,
+// B networks, network b = neurons off[b] .. off[b + 1] - 1, each non-empty. B > 1:
+// c->d_off already holds the offsets (copied on st); B == 1: one network of n
+// neurons, whose box may be given.
+cudaError_t octree_build(relearn_ctx *c, int64_t n, int32_t B, const float *x, const float *y,
                          const float *z, const float *box_lo, const float *box_hi,
                          cudaStream_t st)
 {
     cudaError_t e;
     Box box{};
-    box.given = box_lo && box_hi;
+    box.given = B == 1 && box_lo && box_hi;
     if (box.given)
         for (int a = 0; a < 3; ++a) {
             box.lo[a] = box_lo[a];
             box.hi[a] = box_hi[a];
         }
-    uint32_t *ord = reinterpret_cast<uint32_t *>(c->d_cnt); // 6 words of scratch
-    bbox_init_kernel<<<1, 32, 0, st>>>(ord);
+    const unsigned gn = grid_for(n, 256, c->num_sms);
+    const unsigned gb = (unsigned)((B + 255) / 256);
+    bbox_init_kernel<<<gb, 256, 0, st>>>(c->d_ord, B, B == 1 ? c->d_off : nullptr, n);
     note_launch();
-    bbox_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(x, y, z, n, ord);
+    bbox_kernel<<<gn, 256, 0, st>>>(x, y, z, n, c->d_off, B, c->d_ord);
     note_launch();
-    geom_kernel<<<1, 1, 0, st>>>(ord, box, c->d_geom);
+    geom_kernel<<<gb, 256, 0, st>>>(c->d_ord, box, c->d_geom, B);
     note_launch();
-    morton_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(x, y, z, n, c->d_geom,
-                                                                  c->d_codes, c->d_perm);
+    morton_kernel<<<gn, 256, 0, st>>>(x, y, z, n, c->d_off, B, c->d_geom, c->d_codes, c->d_nkey,
+                                      c->d_perm);
     note_launch();
     int which = 0;
-    if ((e = radix_sort_u32(c->d_codes, c->d_codes_alt, c->d_perm, c->d_perm_alt, n, nullptr, 30,
-                            c->sort, st, &which)))
-        return e;
-    if (which) { // keep the sorted result in the primary buffers
-        if ((e = cudaMemcpyAsync(c->d_codes, c->d_codes_alt, n * sizeof(uint32_t),
-                                 cudaMemcpyDeviceToDevice, st)))
+    if (B == 1) {
+        if ((e = radix_sort_u32(c->d_codes, c->d_codes_alt, c->d_perm, c->d_perm_alt, n, nullptr,
+                                30, c->sort, st, &which)))
             return e;
-        if ((e = cudaMemcpyAsync(c->d_perm, c->d_perm_alt, n * sizeof(int32_t),
-                                 cudaMemcpyDeviceToDevice, st)))
+        if (which) { // keep the sorted result in the primary buffers
+            if ((e = cudaMemcpyAsync(c->d_codes, c->d_codes_alt, n * sizeof(uint32_t),
+                                     cudaMemcpyDeviceToDevice, st)))
+                return e;
+            if ((e = cudaMemcpyAsync(c->d_perm, c->d_perm_alt, n * sizeof(int32_t),
+                                     cudaMemcpyDeviceToDevice, st)))
+                return e;
+        }
+    } else {
+        int bits = 1;
+        while (bits < 31 && (1ll << bits) < B) ++bits;
+        if ((e = radix_sort_u64(c->d_nkey, c->d_nkey_alt, c->d_perm, c->d_perm_alt, n, nullptr,
+                                30 + bits, c->sort, st, &which)))
             return e;
+        if (which && (e = cudaMemcpyAsync(c->d_perm, c->d_perm_alt, n * sizeof(int32_t),
+                                          cudaMemcpyDeviceToDevice, st)))
+            return e;
+        split_keys_kernel<<<gn, 256, 0, st>>>(which ? c->d_nkey_alt : c->d_nkey, n, c->d_codes,
+                                              c->d_net);
+        note_launch();
     }
-    gather_pos_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(x, y, z, c->d_perm, n,
-                                                                      c->d_pos);
+    int32_t *net = B > 1 ? c->d_net : nullptr;
+    gather_pos_kernel<<<gn, 256, 0, st>>>(x, y, z, c->d_perm, n, c->d_pos);
     note_launch();
-    fixed_pos_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(c->d_pos, n, c->d_geom,
-                                                                     c->d_posq);
+    fixed_pos_kernel<<<gn, 256, 0, st>>>(c->d_pos, n, net, c->d_geom, c->d_posq);
     note_launch();
     if ((e = cudaMemsetAsync(c->d_mask, 0, n * sizeof(uint32_t), st))) return e;
-    topo_pairs_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(c->d_codes, n, c->d_mask);
+    topo_pairs_kernel<<<gn, 256, 0, st>>>(c->d_codes, net, c->d_off, n, c->d_mask);
     note_launch();
     topo_count_kernel<<<grid_for(n + 1, 256, c->num_sms), 256, 0, st>>>(c->d_mask, n, c->d_cnt);
     note_launch();
     if ((e = scan_exclusive(c->d_cnt, c->d_base, n + 1, nullptr, c->d_i64 + I64_NODES, c->scan,
                             st)))
         return e;
-    topo_emit_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(
-        c->d_codes, n, c->d_mask, c->d_base, c->d_nodes, c->d_parent, c->d_nsize, c->d_leaf);
+    topo_emit_kernel<<<gn, 256, 0, st>>>(c->d_codes, net, c->d_off, n, c->d_mask, c->d_base,
+                                         c->d_nodes, c->d_parent, c->d_nsize, c->d_leaf);
+    note_launch();
+    roots_kernel<<<gb, 256, 0, st>>>(c->d_base, c->d_off, B, c->d_root);
     note_launch();
     return cudaGetLastError();
 }
@@ -541,7 +637,8 @@ cudaError_t octree_reduce(relearn_ctx *c, const int32_t *vac_de, cudaStream_t st
                                                         c->d_pos, c->d_posq, vac_de, n, bsum, P);
     note_launch();
     reduce_nodes_kernel<<<grid_for(c->max_nodes, 256, c->num_sms), 256, 0, st>>>(
-        c->d_nodes, c->d_nsize, c->d_i64 + I64_NODES, P, c->d_geom);
+        c->d_nodes, c->d_nsize, c->d_i64 + I64_NODES, P, c->num_nets > 1 ? c->d_net : nullptr,
+        c->d_geom);
     note_launch();
     return cudaGetLastError();
 }
@@ -649,13 +746,14 @@ extern "C" relearn_status relearn_morton_order_noalloc(int64_t n, const float *x
             box.hi[a] = box_hi3[a];
         }
     const unsigned grid = grid_for(n, 256, d.num_sms);
-    bbox_init_kernel<<<1, 32, 0, st>>>(ord); // geom_kernel reads the bounding box
+    // One network: the box and Morton kernels never read the network offsets.
+    bbox_init_kernel<<<1, 32, 0, st>>>(ord, 1, nullptr, n); // geom_kernel reads the box
     note_launch();
-    bbox_kernel<<<grid, 256, 0, st>>>(x, y, z, n, ord);
+    bbox_kernel<<<grid, 256, 0, st>>>(x, y, z, n, nullptr, 1, ord);
     note_launch();
-    geom_kernel<<<1, 1, 0, st>>>(ord, box, geom);
+    geom_kernel<<<1, 1, 0, st>>>(ord, box, geom, 1);
     note_launch();
-    morton_kernel<<<grid, 256, 0, st>>>(x, y, z, n, geom, codes, perm);
+    morton_kernel<<<grid, 256, 0, st>>>(x, y, z, n, nullptr, 1, geom, codes, nullptr, perm);
     note_launch();
     int which = 0;
     if (radix_sort_u32(codes, codes_alt, perm, perm_alt, n, nullptr, 30, ss, st, &which) !=

@@ -47,12 +47,25 @@ constexpr int kSpreadDepth8 = 4;
 
 // A node of depth d is accepted iff d^2 > thr0 / 4^d, thr0 = (root length / theta)^2
 // rounded to FP32 (see NodeTopo::shift). theta = 0 accepts no inner node.
-__global__ void search_const_kernel(const Geom *g, float sigma, float theta, SearchConst *sc)
+// One thread per network; per-network sigma/theta replace the scalars when given.
+__global__ void search_const_kernel(const Geom *g_all, int32_t B, float sigma, float theta,
+                                    const float *net_sigma, const float *net_theta,
+                                    SearchConst *sc_all, int32_t *status)
 {
-    const double ext = g->ext, th = (double)theta;
+    const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    float sg = net_sigma ? net_sigma[b] : sigma;
+    float tt = net_theta ? net_theta[b] : theta;
+    if (!(sg > 0.0f && sg < 3.0e38f && tt >= 0.0f && tt < 3.0e38f)) {
+        set_status(status, RELEARN_ERR_INVALID_ARG); // the update applies nothing
+        sg = 1.0f;
+        tt = 0.0f;
+    }
+    const double ext = g_all[b].ext, th = (double)tt;
     const float thr0 = th > 0.0 ? (float)((ext / th) * (ext / th)) : 3.4028234663852886e38f;
+    SearchConst *sc = sc_all + b;
     sc->thr0 = __float_as_uint(fminf(thr0, 3.4028234663852886e38f));
-    const double s = (double)sigma;
+    const double s = (double)sg;
     sc->k2 = (float)(1.4426950408889634 / (s * s));
 }
 
@@ -75,7 +88,8 @@ __global__ void query_counts_kernel(const int32_t *__restrict__ vac_ax,
     }
 }
 
-// Q = total searches; beyond capacity the update is void (status CAPACITY).
+// Q = total searches; beyond capacity the update is void (status CAPACITY), and so
+// it is while an earlier device error (e.g. a bad per-network parameter) is unread.
 __global__ void query_check_kernel(const int64_t *d_total, const int64_t *d_active,
                                    int64_t max_searches, int32_t *d_Q, int32_t *d_A,
                                    int64_t *d_Qout, int64_t *d_Qsum, int32_t *status)
@@ -83,8 +97,8 @@ __global__ void query_check_kernel(const int64_t *d_total, const int64_t *d_acti
     int64_t q = *d_total;
     int64_t a = *d_active;
     *d_Qout = q;
-    if (q > max_searches) {
-        set_status(status, RELEARN_ERR_CAPACITY);
+    if (q > max_searches) set_status(status, RELEARN_ERR_CAPACITY);
+    if (*(volatile int32_t *)status != 0) {
         q = 0;
         a = 0;
     }
@@ -124,7 +138,9 @@ struct SearchArgs {
     const int32_t *__restrict__ vac_ax;
     const int32_t *__restrict__ qoff_o;
     const int32_t *d_A;
-    const SearchConst *sc;
+    const SearchConst *sc; // [networks]
+    const int32_t *net;    // network of each Morton position, NULL for one network
+    const int32_t *root;   // root node of each network
     int32_t *work;
     int32_t *req_tgt;
     int64_t *failed;
@@ -242,10 +258,7 @@ __device__ __forceinline__ int32_t find_root(const Node *__restrict__ nodes, int
 #endif
 __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kernel(SearchArgs a)
 {
-    const uint32_t thr0 = __ldg(&a.sc->thr0);
-    const float k2 = __ldg(&a.sc->k2);
     const int32_t A = *a.d_A;
-    const int32_t root_end = __ldg(&a.nodes[0].t.escape);
     const int lane = threadIdx.x & 31;
     int64_t my_evals = 0, my_steps = 0;
     int32_t ckp[kMaxCk];
@@ -262,24 +275,45 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
         const float4 xp = live ? a.pos[s] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float3 x = make_float3(xp.x, xp.y, xp.z);
         const int32_t self_node = live ? a.leaf_of[s] : -1;
+        const int last = min(A - 1 - nb, 31);
+        // this lane's network (an idle lane takes the last live lane's): its root, the
+        // end of its subtree, its acceptance threshold and kernel width
+        int32_t net = a.net && live ? a.net[s] : 0;
+        net = __shfl_sync(0xffffffffu, net, live ? lane : last);
+        const int32_t root = __ldg(&a.root[net]);
+        const int32_t root_end = __ldg(&a.nodes[root].t.escape);
+        const uint32_t thr0 = __ldg(&a.sc[net].thr0);
+        const float k2 = __ldg(&a.sc[net].k2);
 
         // ---- walk width: Morton codes are sorted, so the first and last code of a
-        // range bound the cell that holds all of it
+        // range bound the cell that holds all of it; a union never spans two networks
         int G = a.forced_group;
+        const int32_t n0 = __shfl_sync(0xffffffffu, net, 0);
+        const int32_t n31 = __shfl_sync(0xffffffffu, net, 31);
+        const int32_t nf = __shfl_sync(0xffffffffu, net, lane & ~7);
+        const int32_t nl = __shfl_sync(0xffffffffu, net, lane | 7);
+        const bool mixed8 = __any_sync(0xffffffffu, nf != nl);
         if (G == 0) {
-            const int last = min(A - 1 - nb, 31);
             uint32_t code = live ? a.codes[s] : 0u;
             code = __shfl_sync(0xffffffffu, code, live ? lane : last);
             const uint32_t c0 = __shfl_sync(0xffffffffu, code, 0);
             const uint32_t c31 = __shfl_sync(0xffffffffu, code, 31);
-            if (morton_common_digits(c0, c31) >= a.spread_depth) {
+            if (n0 == n31 && morton_common_digits(c0, c31) >= a.spread_depth) {
                 G = 32;
             } else {
                 const uint32_t f = __shfl_sync(0xffffffffu, code, lane & ~7);
                 const uint32_t l = __shfl_sync(0xffffffffu, code, lane | 7);
                 const int cp8 = __reduce_min_sync(0xffffffffu, morton_common_digits(f, l));
-                G = cp8 >= a.spread_depth8 ? 8 : 1;
+                G = !mixed8 && cp8 >= a.spread_depth8 ? 8 : 1;
             }
+        } else if (G > 1 && n0 != n31) {
+            // a fixed width whose groups would span networks: the widest that does not
+            const int32_t nh = __shfl_sync(0xffffffffu, net, lane & ~15);
+            const int32_t nt = __shfl_sync(0xffffffffu, net, lane | 15);
+            const bool mixed16 = __any_sync(0xffffffffu, nh != nt);
+            G = G == 32 ? (mixed16 ? (mixed8 ? 1 : 8) : 16) : G == 16 && mixed16 ? (mixed8 ? 1 : 8)
+                                                                                : G;
+            if (G == 8 && mixed8) G = 1;
         }
         const uint32_t gmask =
             G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
@@ -289,7 +323,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
         double S = 0.0; // the root-level normaliser, FP64
         int32_t own = 0, nck = 0;
         for (int attempt = 0; attempt < 2; ++attempt) {
-            int32_t p = 1, skip = live ? 0 : 0x7fffffff, steps = 0;
+            int32_t p = root + 1, skip = live ? 0 : 0x7fffffff, steps = 0;
             float cum = 0.0f, comp = 0.0f; // Kahan sum and compensation
             own = 0;
             nck = 0;
@@ -354,8 +388,8 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
             const bool redo = live && S < (double)kTiny;
             if (!__any_sync(0xffffffffu, redo)) break;
             if (redo) {
-                const WalkOut w = walk<false>(a.nodes, 1, root_end, 0.0f, x, self_node, thr0, k2,
-                                              k2sh, 0.0f);
+                const WalkOut w = walk<false>(a.nodes, root + 1, root_end, 0.0f, x, self_node,
+                                              thr0, k2, k2sh, 0.0f);
                 if (w.dmin2 < __int_as_float(0x7f800000)) k2sh = __fmul_rn(k2, w.dmin2);
             }
         }
@@ -384,8 +418,8 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                 int32_t k = find_root(a.nodes, ckp[lo], root_end, ckc[lo], ckk[lo], x, self_node,
                                       thr0, k2, k2sh, (float)tgt);
                 if (k < 0) // u * S rounded up to S past the last weighted candidate
-                    k = find_root(a.nodes, 1, root_end, 0.0f, 0.0f, x, self_node, thr0, k2, k2sh,
-                                  __int_as_float(0x7f800000));
+                    k = find_root(a.nodes, root + 1, root_end, 0.0f, 0.0f, x, self_node, thr0,
+                                  k2, k2sh, __int_as_float(0x7f800000));
                 draws = 1;
                 while (k >= 0 && draws < 24) {
                     const int4 tk = __ldg(reinterpret_cast<const int4 *>(&a.nodes[k].t));
@@ -457,7 +491,9 @@ cudaError_t search_prepare(relearn_ctx *c, const relearn_params &p, const int32_
 {
     cudaError_t e;
     const int64_t n = c->n;
-    search_const_kernel<<<1, 1, 0, st>>>(c->d_geom, p.sigma, p.theta, c->d_sc);
+    search_const_kernel<<<(c->num_nets + 255) / 256, 256, 0, st>>>(
+        c->d_geom, c->num_nets, p.sigma, p.theta, p.net_sigma, p.net_theta, c->d_sc,
+        c->d_status);
     note_launch();
     int32_t *active = c->d_cnt, *cnt_o = c->d_tcnt; // scratch
     query_counts_kernel<<<grid_for(n + 1, 256, c->num_sms), 256, 0, st>>>(vac_ax, c->d_perm, n,
@@ -497,6 +533,8 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     a.qoff_o = c->d_qoff_o;
     a.d_A = c->d_i32 + I32_ACTIVE;
     a.sc = c->d_sc;
+    a.net = c->num_nets > 1 ? c->d_net : nullptr;
+    a.root = c->d_root;
     a.work = c->d_i32 + I32_WORK;
     a.req_tgt = c->d_req_tgt;
     a.failed = c->d_i64 + I64_FAILED;

@@ -38,7 +38,8 @@ class RelearnError(RuntimeError):
 class relearn_params(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_float), ("theta", ctypes.c_float), ("seed", ctypes.c_uint64),
                 ("step", ctypes.c_uint64), ("flags", ctypes.c_uint32),
-                ("search_group", ctypes.c_uint32)]
+                ("search_group", ctypes.c_uint32), ("net_sigma", ctypes.c_void_p),
+                ("net_theta", ctypes.c_void_p)]
 
 
 class relearn_update_stats(ctypes.Structure):
@@ -59,8 +60,11 @@ _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _SIGS = {
     "relearn_create": [ctypes.POINTER(_P), ctypes.c_int, _I64, _I64, _I64],
+    "relearn_create_batched": [ctypes.POINTER(_P), ctypes.c_int, _I64, _I64, _I64,
+                               ctypes.c_int32],
     "relearn_destroy": [_P],
     "relearn_build_octree": [_P, _I64, _P, _P, _P, _P, _P, _P, _P],
+    "relearn_build_octree_batch": [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P],
     "relearn_update_connectivity": [_P, ctypes.POINTER(relearn_params), _P, _P, _P,
                                     ctypes.POINTER(relearn_update_stats), _P],
     "relearn_delete_synapses": [_P, ctypes.POINTER(relearn_params), _P, _P, _P, _P,
@@ -146,6 +150,8 @@ class Context:
         self.max_synapses = max_synapses
         self.max_searches = max_searches
         self.n = 0
+        self.num_networks = 1
+        self.keep = ()  # device arrays a params struct points at (per-network sigma/theta)
 
     def close(self):
         if self.handle:
@@ -170,9 +176,14 @@ def _raise(ctx, status, where):
     raise RelearnError(status, where, msg)
 
 
-def params(sigma, theta, seed, step, flags=0, search_group=0):
+def params(sigma, theta, seed, step, flags=0, search_group=0, net_sigma=None, net_theta=None):
+    """net_sigma / net_theta: optional float32 CUDA tensors, one value per network; the
+    caller keeps them alive while the params are in use."""
+    torch = _torch() if (net_sigma is not None or net_theta is not None) else None
+    ps = None if net_sigma is None else _dev_ptr(net_sigma, torch.float32, None, "net_sigma")
+    pt = None if net_theta is None else _dev_ptr(net_theta, torch.float32, None, "net_theta")
     return relearn_params(float(sigma), float(theta), int(seed), int(step), int(flags),
-                          int(search_group))
+                          int(search_group), ps, pt)
 
 
 # ------------------------------------------------------------------ entry points
@@ -184,6 +195,17 @@ def relearn_create(max_neurons, max_synapses, max_searches=0, device=None):
                               int(max_searches))
     if st != OK:
         raise RelearnError(st, "relearn_create")
+    return Context(h, dev, int(max_neurons), int(max_synapses), int(max_searches))
+
+
+def relearn_create_batched(max_neurons, max_synapses, max_networks, max_searches=0, device=None):
+    torch = _torch()
+    dev = torch.cuda.current_device() if device is None else int(device)
+    h = ctypes.c_void_p()
+    st = lib().relearn_create_batched(ctypes.byref(h), dev, int(max_neurons), int(max_synapses),
+                                      int(max_searches), int(max_networks))
+    if st != OK:
+        raise RelearnError(st, "relearn_create_batched")
     return Context(h, dev, int(max_neurons), int(max_synapses), int(max_searches))
 
 
@@ -208,6 +230,27 @@ def relearn_build_octree(ctx, x, y, z, vac_de=None, box_lo=None, box_hi=None, st
                                     _stream(stream))
     _raise(ctx, st, "relearn_build_octree")
     ctx.n = n
+    ctx.num_networks = 1
+
+
+def relearn_build_octree_batch(ctx, offsets, x, y, z, vac_de=None, stream=None):
+    """offsets: host int64 sequence of num_networks + 1 entries (0 .. n)."""
+    torch = _torch()
+    off = np.ascontiguousarray(offsets, np.int64)
+    if off.ndim != 1 or off.size < 2:
+        raise ValueError("offsets: need num_networks + 1 entries")
+    n = int(off[-1])
+    if x.numel() < n:
+        raise ValueError("x: fewer positions than offsets[-1]")
+    px = _dev_ptr(x, torch.float32, n, "x")
+    py = _dev_ptr(y, torch.float32, n, "y")
+    pz = _dev_ptr(z, torch.float32, n, "z")
+    pv = None if vac_de is None else _dev_ptr(vac_de, torch.int32, n, "vac_de")
+    st = lib().relearn_build_octree_batch(ctx.handle, int(off.size - 1), _np_ptr(off), px, py,
+                                          pz, pv, _stream(stream))
+    _raise(ctx, st, "relearn_build_octree_batch")
+    ctx.n = n
+    ctx.num_networks = int(off.size - 1)
 
 
 def relearn_update_connectivity(ctx, prm, vac_ax, vac_de, type_, stats=False, stream=None):

@@ -15,6 +15,11 @@ below stand in for it:
   2^14 per cluster, is the headline benchmark workload).
 * ``cortical_slab``  - 20 x 20 x 2.5 mm slab of 10 layers, uniform within a layer,
   layer shares 1 + U(-0.3, 0.3) normalised, Poisson(1) vacancies (2^24 neurons).
+* ``network_batch``  - many independent networks of uneven sizes (log-uniform
+  neuron counts), each uniform in its own cube at the density of ``uniform_cube``
+  (4096 neurons per mm^3), Poisson(2) vacancies clipped to 0..8, per-network sigma
+  uniform in [500, 1000] um (256 networks of 10^3 .. 10^6 neurons, about 3.7e7 in
+  total, is the batched workload).
 
 Every generator is keyed by an integer seed through NumPy's Philox bit
 generator; 20 % of neurons are inhibitory (type 1), drawn i.i.d.
@@ -122,3 +127,62 @@ def regrowth(n, seed, step, lam=1.0):
     rng = _rng(seed, 9000 + int(step))
     return (np.minimum(rng.poisson(lam, n), 8).astype(np.int32),
             np.minimum(rng.poisson(lam, n), 8).astype(np.int32))
+
+
+@dataclass
+class NetworkBatch:
+    """Independent networks packed into one id range: network b holds the ids
+    offsets[b] .. offsets[b + 1] - 1."""
+    name: str
+    offsets: np.ndarray    # int64 [B + 1]
+    x: np.ndarray          # float32 [n], each network in its own frame
+    y: np.ndarray
+    z: np.ndarray
+    vac_ax: np.ndarray
+    vac_de: np.ndarray
+    type: np.ndarray
+    sigma: np.ndarray      # float32 [B], per-network kernel width
+    theta: float
+    seed: int
+    params: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.offsets[-1])
+
+    @property
+    def num_networks(self) -> int:
+        return int(self.offsets.shape[0] - 1)
+
+    def network(self, b: int) -> Network:
+        lo, hi = int(self.offsets[b]), int(self.offsets[b + 1])
+        return Network(f"{self.name}[{b}]", self.x[lo:hi], self.y[lo:hi], self.z[lo:hi],
+                       self.vac_ax[lo:hi], self.vac_de[lo:hi], self.type[lo:hi],
+                       float(self.sigma[b]), self.theta, self.seed, {"id_base": lo})
+
+
+def network_batch(networks=256, n_min=1000, n_max=1000000, seed=4, density_per_mm3=4096.0,
+                  sigma_lo=500.0, sigma_hi=1000.0, theta=0.3, lam=2.0, sizes=None):
+    """``networks`` independent networks, neuron counts log-uniform in [n_min, n_max]
+    (or the given ``sizes``), each uniform in [0, side_b]^3 with side_b chosen for a
+    constant density, sigma_b ~ U[sigma_lo, sigma_hi]."""
+    rng = _rng(seed)
+    if sizes is None:
+        sizes = np.rint(np.exp(rng.uniform(np.log(n_min), np.log(n_max), networks)))
+    sizes = np.asarray(sizes, np.int64)
+    assert sizes.min() >= 1
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(offsets[-1])
+    side = (sizes / density_per_mm3) ** (1.0 / 3.0) * 1000.0  # micrometres
+    owner = np.repeat(np.arange(sizes.shape[0]), sizes)
+    p = (rng.random((3, n)) * side[owner]).astype(np.float32)
+    sigma = rng.uniform(sigma_lo, sigma_hi, sizes.shape[0]).astype(np.float32)
+    return NetworkBatch("network_batch", offsets, p[0].copy(), p[1].copy(), p[2].copy(),
+                        _poisson(rng, lam, n), _poisson(rng, lam, n), _types(rng, n), sigma,
+                        float(theta), int(seed),
+                        {"networks": int(sizes.shape[0]), "n": n,
+                         "sizes": "log-uniform" if n_min != n_max else "equal",
+                         "n_range": [int(sizes.min()), int(sizes.max())],
+                         "density_per_mm3": density_per_mm3,
+                         "sigma_um": [sigma_lo, sigma_hi],
+                         "vacancies": f"Poisson({lam}) clipped 0..8"})

@@ -1,0 +1,243 @@
+"""Batched form on the GPU (relearn_build_octree_batch + per-network sigma) against
+the oracle run network by network. Integers bit-exact outside the FP32/FP64
+exemption (see gpu_common), root-frontier ln S within 1e-5."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import LNS_TOL, compare_targets, dev
+from paper_2509_26193_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+# ragged: a lone neuron, a pair, a triple, sizes around a warp, and a few thousands
+SIZES = [1, 2, 3, 31, 33, 500, 4096, 1200, 64, 2500, 7, 3000]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2509_26193_gb300 import build
+    build.build()
+    oracle.build()
+
+
+class GpuBatch:
+    def __init__(self, b, max_synapses=None, build=True):
+        from paper_2509_26193_gb300 import relearn as R
+        self.R, self.b = R, b
+        cap = max_synapses or int(b.vac_ax.sum()) + 64
+        self.ctx = R.relearn_create_batched(b.n, cap, max(b.num_networks, 1))
+        self.x, self.y, self.z = dev(b.x), dev(b.y), dev(b.z)
+        self.vac_ax, self.vac_de = dev(b.vac_ax), dev(b.vac_de)
+        self.type = dev(b.type)
+        self.sigma = dev(b.sigma)
+        if build:
+            R.relearn_build_octree_batch(self.ctx, b.offsets, self.x, self.y, self.z)
+
+    def update(self, step, group=0, diag=True, sigma=None):
+        R = self.R
+        p = R.params(0.0, self.b.theta, self.b.seed, step, R.FLAG_DIAG if diag else 0, group,
+                     net_sigma=self.sigma if sigma is None else sigma)
+        return R.relearn_update_connectivity(self.ctx, p, self.vac_ax, self.vac_de, self.type,
+                                             stats=True)
+
+    def close(self):
+        self.ctx.close()
+
+
+def _oracle(b, step, syn_cap=None):
+    trees = [oracle.Tree(b.x[lo:hi], b.y[lo:hi], b.z[lo:hi], id_base=lo)
+             for lo, hi in zip(b.offsets[:-1], b.offsets[1:])]
+    va, vd = b.vac_ax.copy(), b.vac_de.copy()
+    syn = oracle.Synapses(syn_cap or int(va.sum()) + 64)
+    r = oracle.update_connectivity_batch(trees, b.offsets, va, vd, b.type, b.sigma, b.theta,
+                                         b.seed, step, syn, threads=8)
+    return r, va, vd, syn
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.0])
+def test_batch_search_matches_oracle(theta):
+    from paper_2509_26193_gb300 import relearn as R
+    b = workloads.network_batch(sizes=SIZES, seed=21, theta=theta)
+    g = GpuBatch(b)
+    stats = g.update(step=4)
+    gt, gacc = R.relearn_get_requests(g.ctx)
+    r, va, vd, syn = _oracle(b, 4)
+    assert stats["searches"] == len(r["tgt"]) == len(gt)
+    bad, exempt, exempt_diff = compare_targets(gt, r["tgt"], r["diag"])
+    assert bad == 0, (bad, exempt, exempt_diff)
+    assert exempt_diff <= max(2, exempt // 10)
+    dg = R.relearn_get_search_diag(g.ctx)
+    od = r["diag"]
+    fin = np.isfinite(od["ln_s0"])
+    assert np.array_equal(np.isfinite(dg["ln_s0"]), fin)
+    assert np.abs(dg["ln_s0"][fin] - od["ln_s0"][fin]).max() < LNS_TOL
+    same = gt == r["tgt"]
+    assert np.mean(dg["evals"][same] == od["evals"][same]) > 0.99
+    if exempt_diff == 0:  # then accept, vacancies and store are bit-exact too
+        assert np.array_equal(gacc, r["accept"])
+        ga, gd = g.vac_ax.cpu().numpy(), g.vac_de.cpu().numpy()
+        assert np.array_equal(ga, va) and np.array_equal(gd, vd)
+        s, d, sg = R.relearn_get_synapses(g.ctx)
+        os_, od_, osg = syn.arrays()
+        assert np.array_equal(s, os_) and np.array_equal(d, od_) and np.array_equal(sg, osg)
+    g.close()
+
+
+def test_batch_tree_matches_per_network_builds():
+    """The batched topology is the concatenation of the per-network trees."""
+    from paper_2509_26193_gb300 import relearn as R
+    b = workloads.network_batch(sizes=SIZES, seed=22)
+    g = GpuBatch(b, build=False)
+    R.relearn_build_octree_batch(g.ctx, b.offsets, g.x, g.y, g.z, g.vac_de)
+    tree = R.relearn_get_tree(g.ctx)
+    at = 0
+    for k in range(b.num_networks):
+        lo, hi = int(b.offsets[k]), int(b.offsets[k + 1])
+        if hi - lo == 1:
+            # a lone neuron: the GPU keeps an inner root above its leaf (every network's
+            # search starts below its root); the oracle's root is the leaf itself
+            assert tree["depth"][at] == 0 and tree["is_leaf"][at] == 0
+            assert tree["is_leaf"][at + 1] == 1 and tree["neuron"][at + 1] == lo
+            assert tree["first"][at] == lo and tree["size"][at] == 1
+            at += 2
+            continue
+        t = oracle.Tree(b.x[lo:hi], b.y[lo:hi], b.z[lo:hi], id_base=lo)
+        t.reduce(b.vac_de[lo:hi])
+        e = t.export(compressed=True)
+        m = len(e["depth"])
+        for key in ("depth", "size", "is_leaf"):
+            assert np.array_equal(tree[key][at:at + m], e[key]), (k, key)
+        assert np.array_equal(tree["first"][at:at + m], e["first"] + lo)
+        leaf = e["is_leaf"] == 1
+        assert np.array_equal(tree["neuron"][at:at + m][leaf], e["neuron"][leaf] + lo)
+        assert np.array_equal(tree["count"][at:at + m], e["count"].astype(np.int64))
+        has = e["count"] > 0
+        for c in ("cx", "cy", "cz"):
+            got, want = tree[c][at:at + m][has], e[c][has]
+            assert np.all(np.abs(got - want) <= 1e-6 * np.maximum(np.abs(want), 1.0)), (k, c)
+        at += m
+    assert at == len(tree["depth"])
+    g.close()
+
+
+def test_batch_of_one_equals_plain_build():
+    from paper_2509_26193_gb300 import relearn as R
+    net = workloads.uniform_cube(n=4096, seed=1)
+    out = []
+    for batched in (False, True):
+        ctx = R.relearn_create_batched(net.n, 4 * int(net.vac_ax.sum()), 1)
+        x, y, z = dev(net.x), dev(net.y), dev(net.z)
+        va, vd, ty = dev(net.vac_ax), dev(net.vac_de), dev(net.type)
+        if batched:
+            R.relearn_build_octree_batch(ctx, [0, net.n], x, y, z)
+        else:
+            R.relearn_build_octree(ctx, x, y, z)
+        p = R.params(net.sigma, net.theta, net.seed, 1, R.FLAG_DIAG)
+        st = R.relearn_update_connectivity(ctx, p, va, vd, ty, stats=True)
+        out.append((R.relearn_get_requests(ctx), R.relearn_get_synapses(ctx), st["formed"]))
+        ctx.close()
+    (t0, a0), s0, f0 = out[0]
+    (t1, a1), s1, f1 = out[1]
+    assert np.array_equal(t0, t1) and np.array_equal(a0, a1) and f0 == f1
+    for u, v in zip(s0, s1):
+        assert np.array_equal(u, v)
+
+
+def test_batch_results_do_not_depend_on_search_group():
+    from paper_2509_26193_gb300 import relearn as R
+    b = workloads.network_batch(sizes=SIZES, seed=23)
+    got = []
+    for group in (1, 8, 16, 32, 0, 1503):
+        g = GpuBatch(b)
+        g.update(step=6, group=group)
+        tgt, acc = R.relearn_get_requests(g.ctx)
+        dg = R.relearn_get_search_diag(g.ctx)
+        got.append((tgt, acc, dg["ln_s0"], dg["evals"]))
+        g.close()
+    for other in got[1:]:
+        for a, c in zip(got[0], other):
+            assert np.array_equal(a, c)
+
+
+def test_bad_network_sigma_is_reported_and_nothing_applied():
+    import torch
+    from paper_2509_26193_gb300 import relearn as R
+    b = workloads.network_batch(sizes=[100, 200, 300], seed=24)
+    g = GpuBatch(b)
+    bad = g.sigma.clone()
+    bad[1] = 0.0
+    with pytest.raises(R.RelearnError) as ei:
+        g.update(step=0, sigma=bad)
+    assert ei.value.status == R.ERR_INVALID_ARG
+    assert torch.equal(g.vac_ax.cpu(), torch.from_numpy(b.vac_ax))
+    assert torch.equal(g.vac_de.cpu(), torch.from_numpy(b.vac_de))
+    assert len(R.relearn_get_synapses(g.ctx)[0]) == 0
+    # the status was consumed: a good update then runs normally
+    st = g.update(step=0)
+    assert st["formed"] > 0
+    g.close()
+
+
+def test_bad_offsets_are_rejected_on_the_host():
+    from paper_2509_26193_gb300 import relearn as R
+    b = workloads.network_batch(sizes=[10, 20, 30], seed=25)
+    g = GpuBatch(b, build=False)
+    for off in ([1, 10, 30, 60], [0, 10, 10, 60], [0, 20, 10, 60], [0, 10, 30, 61], [0]):
+        with pytest.raises((R.RelearnError, ValueError)):
+            R.relearn_build_octree_batch(g.ctx, off, g.x, g.y, g.z)
+    small = R.relearn_create_batched(b.n, 64, 2)
+    with pytest.raises(R.RelearnError):
+        R.relearn_build_octree_batch(small, b.offsets, g.x, g.y, g.z)  # 3 > max_networks
+    small.close()
+    g.close()
+
+
+def test_batch_step_in_a_cuda_graph_matches_direct_calls():
+    """Build + update + full deletion captured once and replayed: same requests and
+    vacancies as the same calls made directly."""
+    import torch
+    from paper_2509_26193_gb300 import relearn as R
+    b = workloads.network_batch(sizes=SIZES, seed=26)
+    big = np.full(b.n, 1 << 20, np.int32)
+
+    def run(g, step):
+        g.vac_ax.copy_(va0)
+        g.vac_de.copy_(vd0)
+        R.relearn_build_octree_batch(g.ctx, b.offsets, g.x, g.y, g.z)
+        p = R.params(0.0, b.theta, b.seed, step, 0, 0, net_sigma=g.sigma)
+        R.relearn_update_connectivity(g.ctx, p, g.vac_ax, g.vac_de, g.type)
+        tgt_copy.copy_(req_probe(g))
+        R.relearn_delete_synapses(g.ctx, p, retract, retract, g.vac_ax, g.vac_de)
+
+    va0, vd0, retract = dev(b.vac_ax), dev(b.vac_de), dev(big)
+    # direct
+    g1 = GpuBatch(b, build=False)
+    tgt_copy = torch.empty(b.n, dtype=torch.int32, device="cuda")
+    req_probe = lambda g: g.vac_ax  # vacancies after the update, before deletion
+    run(g1, 9)
+    torch.cuda.synchronize()
+    direct = tgt_copy.clone()
+    direct_req = R.relearn_get_requests(g1.ctx)
+    g1.close()
+    # captured
+    g2 = GpuBatch(b, build=False)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        run(g2, 9)  # warm-up outside the graph
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        run(g2, 9)
+    tgt_copy.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(tgt_copy, direct)
+    t2, a2 = R.relearn_get_requests(g2.ctx)
+    assert np.array_equal(t2, direct_req[0]) and np.array_equal(a2, direct_req[1])
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(tgt_copy, direct)
+    g2.close()
