@@ -256,10 +256,22 @@ __device__ __forceinline__ int32_t find_root(const Node *__restrict__ nodes, int
 #ifndef RELEARN_SEARCH_MIN_BLOCKS
 #define RELEARN_SEARCH_MIN_BLOCKS 6 // 40 registers: 6 blocks of 256 threads per SM
 #endif
+// kBatched: several networks, each source walks its own network's tree (root,
+// subtree end, threshold and kernel width looked up per work item); else one
+// network whose constants are loaded once.
+template <bool kBatched>
 __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kernel(SearchArgs a)
 {
     const int32_t A = *a.d_A;
     const int lane = threadIdx.x & 31;
+    int32_t root = 0, root_end = 0;
+    uint32_t thr0 = 0;
+    float k2 = 0.0f;
+    if constexpr (!kBatched) {
+        root_end = __ldg(&a.nodes[0].t.escape);
+        thr0 = __ldg(&a.sc->thr0);
+        k2 = __ldg(&a.sc->k2);
+    }
     int64_t my_evals = 0, my_steps = 0;
     int32_t ckp[kMaxCk];
     float ckc[kMaxCk];  // compensated running sum at each checkpoint
@@ -276,23 +288,27 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
         const float3 x = make_float3(xp.x, xp.y, xp.z);
         const int32_t self_node = live ? a.leaf_of[s] : -1;
         const int last = min(A - 1 - nb, 31);
-        // this lane's network (an idle lane takes the last live lane's): its root, the
-        // end of its subtree, its acceptance threshold and kernel width
-        int32_t net = a.net && live ? a.net[s] : 0;
-        net = __shfl_sync(0xffffffffu, net, live ? lane : last);
-        const int32_t root = __ldg(&a.root[net]);
-        const int32_t root_end = __ldg(&a.nodes[root].t.escape);
-        const uint32_t thr0 = __ldg(&a.sc[net].thr0);
-        const float k2 = __ldg(&a.sc[net].k2);
+        int32_t net = 0, n0 = 0, n31 = 0;
+        bool mixed8 = false;
+        if constexpr (kBatched) {
+            // this lane's network (an idle lane takes the last live lane's): its root,
+            // the end of its subtree, its acceptance threshold and kernel width
+            net = live ? a.net[s] : 0;
+            net = __shfl_sync(0xffffffffu, net, live ? lane : last);
+            root = __ldg(&a.root[net]);
+            root_end = __ldg(&a.nodes[root].t.escape);
+            thr0 = __ldg(&a.sc[net].thr0);
+            k2 = __ldg(&a.sc[net].k2);
+            n0 = __shfl_sync(0xffffffffu, net, 0);
+            n31 = __shfl_sync(0xffffffffu, net, 31);
+            const int32_t nf = __shfl_sync(0xffffffffu, net, lane & ~7);
+            const int32_t nl = __shfl_sync(0xffffffffu, net, lane | 7);
+            mixed8 = __any_sync(0xffffffffu, nf != nl);
+        }
 
         // ---- walk width: Morton codes are sorted, so the first and last code of a
         // range bound the cell that holds all of it; a union never spans two networks
         int G = a.forced_group;
-        const int32_t n0 = __shfl_sync(0xffffffffu, net, 0);
-        const int32_t n31 = __shfl_sync(0xffffffffu, net, 31);
-        const int32_t nf = __shfl_sync(0xffffffffu, net, lane & ~7);
-        const int32_t nl = __shfl_sync(0xffffffffu, net, lane | 7);
-        const bool mixed8 = __any_sync(0xffffffffu, nf != nl);
         if (G == 0) {
             uint32_t code = live ? a.codes[s] : 0u;
             code = __shfl_sync(0xffffffffu, code, live ? lane : last);
@@ -306,7 +322,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                 const int cp8 = __reduce_min_sync(0xffffffffu, morton_common_digits(f, l));
                 G = !mixed8 && cp8 >= a.spread_depth8 ? 8 : 1;
             }
-        } else if (G > 1 && n0 != n31) {
+        } else if (kBatched && G > 1 && n0 != n31) {
             // a fixed width whose groups would span networks: the widest that does not
             const int32_t nh = __shfl_sync(0xffffffffu, net, lane & ~15);
             const int32_t nt = __shfl_sync(0xffffffffu, net, lane | 15);
@@ -551,7 +567,7 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     a.forced_group = p.search_group < 1000 ? (int)p.search_group : 0;
     a.spread_depth = p.search_group >= 1000 ? (int)((p.search_group - 1000) / 100) : kSpreadDepth;
     a.spread_depth8 = p.search_group >= 1000 ? (int)((p.search_group - 1000) % 100) : kSpreadDepth8;
-    void (*kern)(SearchArgs) = bh_search_kernel;
+    void (*kern)(SearchArgs) = a.net ? bh_search_kernel<true> : bh_search_kernel<false>;
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0))) return e;
     if (per_sm < 1) per_sm = 1;
