@@ -93,6 +93,7 @@ def lib():
                 "orc_delete": (_I64, [_I64, _P, _P, _P, _P, _U64, _U64, _P, _P, _P, _P]),
                 "orc_deliver_spikes": (None, [_I64, _I64, _P, _P, _P, _P, _P]),
                 "orc_deliver_rates": (None, [_I64, _I64, _P, _P, _P, _P, _U64, _U64, _P]),
+                "orc_mean_length": (_D, [_P, _D, _D, _P, _P, _P, _P, _P, _P, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -356,3 +357,23 @@ def update_connectivity_batch(trees, offsets, vac_ax, vac_de, type_, sigmas, the
     acc = accept(n, qi, qe, tgt, vac_de, seed, step)
     formed = apply(qi, tgt, acc, type_, vac_ax, vac_de, syn)
     return {"src": qi, "elem": qe, "tgt": tgt, "accept": acc, "diag": diag, "formed": formed}
+
+
+def mean_length(tree: Tree, sigma, theta, vac_ax, vac_de, grad=True):
+    """Differentiable form: L = sum_i m_i l_i / sum_i m_i, l_i the attraction-weighted
+    mean distance from source i to the centroids of its root frontier (m = vac_ax).
+    The tree must have been reduced with the same vac_de. Returns a dict with
+    mean, ell (per neuron, NaN when excluded) and, with grad, dsigma and the position
+    gradient g (n x 3)."""
+    va = _c(vac_ax, np.int32)
+    vd = _c(vac_de, np.int32)
+    n = tree.n
+    ell = np.zeros(n, np.float64)
+    ds = np.zeros(1, np.float64)
+    g = [np.zeros(n, np.float64) for _ in range(3)] if grad else [None] * 3
+    m = lib().orc_mean_length(tree._h, float(sigma), float(theta), _p(va), _p(vd), _p(ell),
+                              _p(ds), *(_p(a) for a in g))
+    out = {"mean": float(m), "ell": ell, "dsigma": float(ds[0])}
+    if grad:
+        out["g"] = np.stack(g, 1)
+    return out

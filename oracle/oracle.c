@@ -20,6 +20,8 @@
  *   deletion ................ Sec. III-A "Update of synapses", first sub-phase
  *   spike delivery .......... Sec. III-A "Update of electrical activity"
  *   firing-rate delivery .... Sec. IV-B "Approximation of firing rates"
+ *   expected synapse length . the draw distribution of Sec. III-B as a smooth field,
+ *                             with its gradient (not in the paper, R15)
  *
  * Readings where the paper is silent (restated at each function):
  *   R1  domain = bounding box of the positions unless a box is given (anisotropic cells)
@@ -43,6 +45,12 @@
  *   R13 firing-rate delivery: the receiver t decides once per step and per source s
  *       whether s spiked, w = philox({s, t, step, 4}, seed).x, spiked iff
  *       w < rate[s] * 2^32 (exact in FP64); every synapse s -> t then carries that spike
+ *   R14 batched form (not in the paper): a tree may hold one network of a batch whose
+ *       ids start at id_base; its search draws use the global id in the counter
+ *   R15 differentiable form (not in the paper): the expected synapse length of a source
+ *       is the attraction-weighted mean distance to the centroids of its root frontier
+ *       (the first draw's candidates); its gradient treats the criterion and the tree
+ *       topology as constant (see orc_mean_length)
  *
  * Every function here has a pin in the CPU test suite (tests/test_oracle_*.py).
  */
@@ -952,4 +960,130 @@ void orc_deliver_rates(int64_t n, int64_t nsyn, const int32_t *s_src, const int3
         uint32_t w = philox_x((uint32_t)s_src[k], (uint32_t)s_tgt[k], (uint32_t)step, 4u, seed);
         if ((double)w < (double)rate[s_src[k]] * 4294967296.0) input[s_tgt[k]] += s_sign[k];
     }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Differentiable form (not in the paper; reading R15). The expected synapse
+ * length of a source i over its root frontier F_i -- the candidates of its first
+ * draw (Sec. III-B, criterion of Sec. II), own leaf excluded (R6):
+ *   D_ik = |x_i - c_k|^2, d_ik = sqrt(D_ik), a_ik = N_k exp(-D_ik / sigma^2) (R5),
+ *   S_i = sum_k a_ik, q_ik = a_ik / S_i, l_i = sum_k q_ik d_ik,
+ *   L = sum_i m_i l_i / M, M = sum_i m_i over the sources with m_i > 0, S_i > 0
+ * (m = vac_ax: the searches a source makes). Gradients; the criterion and the
+ * tree topology are piecewise constant and contribute nothing:
+ *   dl_i/dsigma = (2 / sigma^3) sum_k q_ik (d_ik - l_i) (D_ik - Dbar_i),
+ *                 Dbar_i = sum_k q_ik D_ik,
+ *   dl_i/dc_k   = q_ik r_ik (2 (d_ik - l_i) / sigma^2 - 1 / d_ik), r = x_i - c_k
+ *                 (the 1/d term is 0 where d = 0),
+ *   dl_i/dx_i   = -sum_k dl_i/dc_k,
+ *   dc_k/dx_j   = w_j / N_k for every neuron j in cell k (w = vac_de: the
+ *                 bottom-up centroid is the w-weighted mean).
+ * ell (per neuron, NAN for excluded sources), dsigma and the position
+ * gradients gx, gy, gz are optional outputs; returns L (NAN when M = 0). */
+/* ------------------------------------------------------------------------- */
+static int root_frontier(const OTree *T, int32_t i, double sigma, double theta, Frontier *F,
+                         double *a, double *S_out)
+{
+    double x[3] = {T->px[i], T->py[i], T->pz[i]};
+    SearchCtx s;
+    memset(&s, 0, sizeof(s));
+    s.sigma2 = sigma * sigma;
+    s.theta2 = theta * theta;
+    s.x = x;
+    s.self = i;
+    s.margin_ac = INFINITY;
+    F->n = 0;
+    if (T->n_nodes == 0 || T->nodes[0].leaf) {
+        *S_out = 0.0;
+        return 0;
+    }
+    expand(T, 0, &s, F);
+    double dmin2 = INFINITY; /* common factor exp(dmin2 / sigma^2): q is unchanged */
+    for (int64_t k = 0; k < F->n; ++k)
+        if (!F->e[k].self && F->e[k].d2 < dmin2) dmin2 = F->e[k].d2;
+    double S = 0.0;
+    for (int64_t k = 0; k < F->n; ++k) {
+        a[k] = F->e[k].self ? 0.0 : F->e[k].count * exp(-(F->e[k].d2 - dmin2) / s.sigma2);
+        S += a[k];
+    }
+    *S_out = S;
+    return 1;
+}
+
+double orc_mean_length(void *t, double sigma, double theta, const int32_t *vac_ax,
+                       const int32_t *vac_de, double *ell, double *dsigma, double *gx,
+                       double *gy, double *gz)
+{
+    const OTree *T = (const OTree *)t;
+    const int64_t n = T->n;
+    double *a = (double *)malloc((size_t)(n + 1) * 2 * sizeof(double));
+    double *lsrc = (double *)malloc((size_t)(n ? n : 1) * sizeof(double));
+    Frontier F = {0};
+    double M = 0.0, sum = 0.0, sdsig = 0.0;
+    /* pass 1: l_i and dl_i/dsigma */
+    for (int64_t i = 0; i < n; ++i) {
+        lsrc[i] = NAN;
+        if (vac_ax[i] <= 0) continue;
+        double S;
+        root_frontier(T, (int32_t)i, sigma, theta, &F, a, &S);
+        if (!(S > 0.0)) continue;
+        double l = 0.0, Db = 0.0;
+        for (int64_t k = 0; k < F.n; ++k) {
+            double q = a[k] / S;
+            l += q * sqrt(F.e[k].d2);
+            Db += q * F.e[k].d2;
+        }
+        double cov = 0.0;
+        for (int64_t k = 0; k < F.n; ++k)
+            cov += a[k] / S * (sqrt(F.e[k].d2) - l) * (F.e[k].d2 - Db);
+        lsrc[i] = l;
+        M += vac_ax[i];
+        sum += vac_ax[i] * l;
+        sdsig += vac_ax[i] * 2.0 / (sigma * sigma * sigma) * cov;
+    }
+    if (ell) memcpy(ell, lsrc, (size_t)n * sizeof(double));
+    if (dsigma) *dsigma = M > 0 ? sdsig / M : NAN;
+    if (gx && gy && gz) {
+        /* pass 2: dL/dc_k accumulated per node (G), direct terms per source */
+        double *G = (double *)calloc((size_t)(T->n_nodes ? T->n_nodes : 1) * 3, sizeof(double));
+        for (int64_t j = 0; j < n; ++j) gx[j] = gy[j] = gz[j] = 0.0;
+        for (int64_t i = 0; i < n && M > 0; ++i) {
+            if (!(lsrc[i] == lsrc[i])) continue; /* excluded source */
+            double S;
+            root_frontier(T, (int32_t)i, sigma, theta, &F, a, &S);
+            const double w = vac_ax[i] / M, l = lsrc[i];
+            for (int64_t k = 0; k < F.n; ++k) {
+                if (F.e[k].self || a[k] == 0.0) continue;
+                const ONode *nk = &T->nodes[F.e[k].node];
+                double r[3] = {T->px[i] - nk->cx, T->py[i] - nk->cy, T->pz[i] - nk->cz};
+                double d = sqrt(F.e[k].d2);
+                double kap = a[k] / S * (2.0 * (d - l) / (sigma * sigma) - (d > 0 ? 1.0 / d : 0.0));
+                for (int c = 0; c < 3; ++c) {
+                    double g = w * kap * r[c];
+                    G[3 * F.e[k].node + c] += g;
+                    (c == 0 ? gx : c == 1 ? gy : gz)[i] -= g;
+                }
+            }
+        }
+        /* scatter: neuron j gets w_j * sum over the cells that hold it of G_k / N_k */
+        for (int64_t v = 0; v < T->n_nodes; ++v) {
+            const ONode *nv = &T->nodes[v];
+            if (!nv->leaf) continue;
+            int j = nv->neuron;
+            double h[3] = {0, 0, 0};
+            for (int64_t u = v; u >= 0; u = T->nodes[u].parent) {
+                const ONode *nu = &T->nodes[u];
+                if (nu->count > 0)
+                    for (int c = 0; c < 3; ++c) h[c] += G[3 * u + c] / nu->count;
+            }
+            gx[j] += vac_de[j] * h[0];
+            gy[j] += vac_de[j] * h[1];
+            gz[j] += vac_de[j] * h[2];
+        }
+        free(G);
+    }
+    free(F.e);
+    free(a);
+    free(lsrc);
+    return M > 0 ? sum / M : NAN;
 }

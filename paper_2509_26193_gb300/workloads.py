@@ -15,6 +15,9 @@ below stand in for it:
   2^14 per cluster, is the headline benchmark workload).
 * ``cortical_slab``  - 20 x 20 x 2.5 mm slab of 10 layers, uniform within a layer,
   layer shares 1 + U(-0.3, 0.3) normalised, Poisson(1) vacancies (2^24 neurons).
+* ``differentiable_cube`` - uniform positions in a cube, Poisson(2) vacancies
+  clipped to 0..8, sigma 800 um (2^18 neurons in a 4 mm cube is the
+  differentiable form's workload; smaller n keeps the density by default).
 * ``network_batch``  - many independent networks of uneven sizes (log-uniform
   neuron counts), each uniform in its own cube at the density of ``uniform_cube``
   (4096 neurons per mm^3), Poisson(2) vacancies clipped to 0..8, per-network sigma
@@ -71,6 +74,19 @@ def uniform_cube(n=4096, side=1000.0, seed=1, sigma=750.0, theta=0.3, vac_max=4)
     return Network("uniform_cube", p[0].copy(), p[1].copy(), p[2].copy(), vac_ax, vac_de,
                    _types(rng, n), float(sigma), float(theta), int(seed),
                    {"n": n, "side_um": side, "vacancies": f"U{{0..{vac_max}}}"})
+
+
+def differentiable_cube(n=1 << 18, side=None, seed=5, sigma=800.0, theta=0.3, lam=2.0):
+    """Positions uniform in [0, side]^3; side defaults to 4 mm at 2^18 neurons and keeps
+    that density at other n (1 mm at 2^12)."""
+    if side is None:
+        side = 4000.0 * (n / float(1 << 18)) ** (1.0 / 3.0)
+    rng = _rng(seed)
+    p = (rng.random((3, n)) * side).astype(np.float32)
+    return Network("differentiable_cube", p[0].copy(), p[1].copy(), p[2].copy(),
+                   _poisson(rng, lam, n), _poisson(rng, lam, n), _types(rng, n), float(sigma),
+                   float(theta), int(seed),
+                   {"n": n, "side_um": side, "vacancies": f"Poisson({lam}) clipped 0..8"})
 
 
 def gaussian_clusters(n=1 << 20, clusters=64, side=10000.0, std=300.0, seed=2, sigma=750.0,
