@@ -22,6 +22,13 @@ per-network sigma in [500, 1000] um, theta = 0.3). One step = the batched octree
 build of all networks + one connectivity update of all of them (one search
 launch) + full deletion, captured once in a CUDA graph and replayed; the search
 kernel's walk width is chosen by the autotuner before capture.
+
+--workload diff measures the differentiable form: 2^18 neurons uniform in a
+4 mm cube, Poisson(2) vacancies, sigma = 800 um, theta = 0.3. One step = the
+torch autograd op's forward (octree build, bottom-up update, expected synapse
+length over every source's root frontier) and its hand-written adjoint
+(gradients for sigma and every position); the config also reports the 50 Adam
+steps that calibrate sigma to a 600 um mean length.
 """
 from __future__ import annotations
 
@@ -57,7 +64,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--group", type=int, default=0,
                     help="source neurons per octree walk in the search kernel (0 = default)")
-    ap.add_argument("--workload", choices=["clusters", "batch"], default="clusters")
+    ap.add_argument("--workload", choices=["clusters", "batch", "diff"], default="clusters")
     ap.add_argument("--networks", type=int, default=256)
     return ap.parse_args()
 
@@ -666,12 +673,159 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+# -------------------------------------------------------- differentiable form
+DIFF_METRIC = ("neuron-searches/sec, differentiable form: expected synapse length over the "
+               "root frontier and its adjoint at 2^18 neurons; % of GB300 roofline")
+FLOPS_PER_CAND_FWD, FLOPS_PER_CAND_BWD = 22, 26
+
+
+def diff_cpu_baseline(net):
+    """The FP64 oracle's forward and gradient on the whole 2^18 network, host cores."""
+    import oracle
+    oracle.build()
+    threads = (os.cpu_count() or 1) if oracle.openmp_available() else 1
+    t0 = time.perf_counter()
+    t = oracle.Tree(net.x, net.y, net.z)
+    t.reduce(net.vac_de)
+    oracle.mean_length(t, net.sigma, net.theta, net.vac_ax, net.vac_de, grad=True,
+                       threads=threads)
+    secs = time.perf_counter() - t0
+    units = int(net.vac_ax[net.vac_ax > 0].sum())
+    return {"value": units / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"the whole 2^18 network: tree build, bottom-up update, forward and "
+                      f"FP64 gradient ({secs:.1f} s)"}
+
+
+def run_diff(args):
+    import torch
+    from paper_2509_26193_gb300 import build, relearn as R, workloads
+    from paper_2509_26193_gb300.differentiable import calibrate_sigma, mean_synapse_length
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local if ws > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(device)
+    net = workloads.differentiable_cube()
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = diff_cpu_baseline(net)
+    build.build()
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    x, y, z = (d(a).requires_grad_(True) for a in (net.x, net.y, net.z))
+    va, vd = d(net.vac_ax), d(net.vac_de)
+    sigma = torch.tensor([net.sigma], dtype=torch.float32, device=device, requires_grad=True)
+    ctx = R.relearn_create(net.n, 64, device=device.index)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h = {k: pin(getattr(net, k)) for k in ("x", "y", "z", "vac_ax", "vac_de")}
+    h_out = torch.empty((3, net.n), dtype=torch.float32).pin_memory()
+    units_per_step = int(net.vac_ax[net.vac_ax > 0].sum())
+
+    def step(e2e=False):
+        if e2e:
+            with torch.no_grad():
+                for t, k in ((x, "x"), (y, "y"), (z, "z"), (va, "vac_ax"), (vd, "vac_de")):
+                    t.copy_(h[k], non_blocking=True)
+        for t in (x, y, z, sigma):
+            t.grad = None
+        m = mean_synapse_length(ctx, x, y, z, sigma, va, vd, net.theta)
+        m.backward()
+        if e2e:
+            for k, t in enumerate((x, y, z)):
+                h_out[k].copy_(t.grad, non_blocking=True)
+        return m
+
+    def timed(steps, e2e=False):
+        st = torch.cuda.current_stream()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            step(e2e)
+            b.record(st)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot
+
+    for _ in range(max(args.warmup, 3)):
+        m = step()
+    torch.cuda.synchronize()
+    mean0 = float(m)
+    e0 = R.relearn_get_last_stats(ctx)["length_evals_total"]
+    l0 = R.relearn_launch_count()
+    clocks = ClockSampler(device.index)
+    clocks.start()
+    ms = timed(args.steps)
+    clk = clocks.stop()
+    launches = R.relearn_launch_count() - l0
+    evals = R.relearn_get_last_stats(ctx)["length_evals_total"] - e0
+    units, secs = aggregate(units_per_step * args.steps, ms / 1000.0, ws, device)
+    e2e = None
+    if not args.no_e2e:
+        ms2 = timed(args.steps, e2e=True)
+        u2, s2 = aggregate(units_per_step * args.steps, ms2 / 1000.0, ws, device)
+        e2e = {"value": u2 / s2, "unit": UNIT, "h2d_bytes_per_step": 20 * net.n,
+               "d2h_bytes_per_step": 12 * net.n}
+    # sigma calibration: 50 Adam steps toward a 600 um mean length
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sig, means = calibrate_sigma(ctx, x.detach(), y.detach(), z.detach(), va, vd, net.sigma,
+                                 600.0, steps=50)
+    torch.cuda.synchronize()
+    cal_s = time.perf_counter() - t0
+    if ws > 1:
+        dist.barrier()
+        if rank != 0:
+            dist.destroy_process_group()
+            return
+    peak_tflops = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    flops = evals / 2 * (FLOPS_PER_CAND_FWD + FLOPS_PER_CAND_BWD)
+    achieved = flops / (ms / 1000.0) / 1e12
+    roof = {"bound": "alu", "kernel": "length_kernel (forward + backward)", "achieved": achieved,
+            "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+            "traffic": None,
+            "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop/FMA x "
+                           f"{SM_MAX_MHZ:.0f} MHz (FP32 pipe)",
+            "work": f"{FLOPS_PER_CAND_FWD} flop per candidate forward + {FLOPS_PER_CAND_BWD} "
+                    f"backward x {evals // 2} candidates per pass, over the whole step time "
+                    f"(build and update included: a lower bound for the kernels)"}
+    line = {"metric": DIFF_METRIC, "value": units / secs, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "differentiable_cube n=262144 (uniform 4 mm cube, Poisson(2) "
+                                   "vacancies 0..8, 20% inhibitory)",
+                       "n": net.n, "sigma_um": net.sigma, "theta": net.theta,
+                       "step": "autograd forward (build + bottom-up update + expected length) "
+                               "+ hand-written adjoint (sigma and positions)",
+                       "unit": "searches covered = sum of vac_ax over sources, per fwd+bwd",
+                       "l2": "256 MB flush between steps",
+                       "mean_length_um": mean0,
+                       "candidates_per_source_pass": evals / 2 / args.steps /
+                       max(int((net.vac_ax > 0).sum()), 1),
+                       "calibration": {"steps": 50, "target_um": 600.0,
+                                       "sigma_final_um": float(sig[-1]),
+                                       "mean_final_um": float(means[-1]),
+                                       "seconds": cal_s}},
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "diff":
+        run_diff(args)
     else:
         run_ours(args)
 

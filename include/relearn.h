@@ -102,6 +102,8 @@ typedef struct {
                                    algorithmic work of the search, one per frontier candidate */
     int64_t walk_steps_total;   /* node visits of the grouped root-frontier walks (one node load
                                    per group of source neurons), for the same updates */
+    int64_t length_evals_total; /* frontier candidates visited by the mean-length forward and
+                                   backward kernels since the context was created */
 } relearn_update_stats;
 
 /* Create a context on CUDA device `device` that can hold up to max_neurons
@@ -213,6 +215,40 @@ relearn_status relearn_deliver_spikes(relearn_ctx *ctx, const uint8_t *spiked, i
  *          always spike).  input  device int32[n], written.  step < 2^32. */
 relearn_status relearn_deliver_rates(relearn_ctx *ctx, const float *rate, uint64_t seed,
                                      uint64_t step, int32_t *input, void *stream);
+
+/* Differentiable form (no counterpart in the paper, which only samples partners): the
+ * expected synapse length over the root frontier, a smooth field of sigma and the
+ * positions. For a source i with m_i = vac_ax[i] > 0, F_i = the candidates of its first
+ * draw (the search of relearn_update_connectivity from the root, own leaf excluded);
+ * with D_ik = |x_i - c_k|^2, d_ik = sqrt(D_ik), a_ik = N_k exp(-D_ik / sigma^2):
+ *   l_i = sum_k a_ik d_ik / sum_k a_ik,   mean = sum_i m_i l_i / sum_i m_i,
+ * the sums over the sources whose total attraction is > 0.
+ *   params  sigma and theta (or net_sigma[0] / net_theta[0], device); seed/step unused.
+ *   vac_ax  device int32[n]: the weights m.  vac_de  device int32[n]: N_k and the centroid
+ *           weights (the bottom-up update runs here, Sec. III-B).
+ *   ell     device float[n] or NULL: l_i by neuron id, NaN where excluded.
+ *   mean    device double, written (NaN when no source is included).
+ * FP32 attractions with compensated sums, l and the normaliser in FP64. Needs a
+ * single-network build (STATE otherwise). */
+relearn_status relearn_mean_length(relearn_ctx *ctx, const relearn_params *params,
+                                   const int32_t *vac_ax, const int32_t *vac_de, float *ell,
+                                   double *mean, void *stream);
+
+/* Adjoint of relearn_mean_length (call it right after its forward, same vac_ax and vac_de;
+ * STATE if a build or an update came in between). The acceptance criterion and the tree
+ * topology are piecewise constant and contribute nothing:
+ *   dl_i/dsigma = (2 / sigma^3) sum_k q_ik (d_ik - l_i) (D_ik - Dbar_i),  q = a / S,
+ *   dl_i/dc_k = q_ik r_ik (2 (d_ik - l_i) / sigma^2 - 1 / d_ik),  r = x_i - c_k,
+ *   dl_i/dx_i = -sum_k dl_i/dc_k,  dc_k/dx_j = vac_de[j] / N_k for each neuron j in cell k.
+ *   grad_mean  device double or NULL (= 1): the upstream gradient of mean.
+ *   gx, gy, gz device float[n], written: d(grad_mean * mean)/d(position), by neuron id.
+ *   gsigma     device double or NULL, written: d(grad_mean * mean)/d sigma.
+ * Attractions are recomputed, not stored; the centroid adjoints are accumulated per
+ * node in FP64. */
+relearn_status relearn_mean_length_backward(relearn_ctx *ctx, const int32_t *vac_ax,
+                                            const int32_t *vac_de, const double *grad_mean,
+                                            float *gx, float *gy, float *gz, double *gsigma,
+                                            void *stream);
 
 /* Copy the synapse store to host arrays in canonical order (by source, then target).
  * `count` (host) receives the number stored; src/tgt/sign may be NULL to query only the

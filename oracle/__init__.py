@@ -93,7 +93,7 @@ def lib():
                 "orc_delete": (_I64, [_I64, _P, _P, _P, _P, _U64, _U64, _P, _P, _P, _P]),
                 "orc_deliver_spikes": (None, [_I64, _I64, _P, _P, _P, _P, _P]),
                 "orc_deliver_rates": (None, [_I64, _I64, _P, _P, _P, _P, _U64, _U64, _P]),
-                "orc_mean_length": (_D, [_P, _D, _D, _P, _P, _P, _P, _P, _P, _P]),
+                "orc_mean_length": (_D, [_P, _D, _D, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -359,7 +359,7 @@ def update_connectivity_batch(trees, offsets, vac_ax, vac_de, type_, sigmas, the
     return {"src": qi, "elem": qe, "tgt": tgt, "accept": acc, "diag": diag, "formed": formed}
 
 
-def mean_length(tree: Tree, sigma, theta, vac_ax, vac_de, grad=True):
+def mean_length(tree: Tree, sigma, theta, vac_ax, vac_de, grad=True, threads=1):
     """Differentiable form: L = sum_i m_i l_i / sum_i m_i, l_i the attraction-weighted
     mean distance from source i to the centroids of its root frontier (m = vac_ax).
     The tree must have been reduced with the same vac_de. Returns a dict with
@@ -372,7 +372,7 @@ def mean_length(tree: Tree, sigma, theta, vac_ax, vac_de, grad=True):
     ds = np.zeros(1, np.float64)
     g = [np.zeros(n, np.float64) for _ in range(3)] if grad else [None] * 3
     m = lib().orc_mean_length(tree._h, float(sigma), float(theta), _p(va), _p(vd), _p(ell),
-                              _p(ds), *(_p(a) for a in g))
+                              _p(ds), *(_p(a) for a in g), int(threads))
     out = {"mean": float(m), "ell": ell, "dsigma": float(ds[0])}
     if grad:
         out["g"] = np.stack(g, 1)

@@ -979,7 +979,8 @@ void orc_deliver_rates(int64_t n, int64_t nsyn, const int32_t *s_src, const int3
  *   dc_k/dx_j   = w_j / N_k for every neuron j in cell k (w = vac_de: the
  *                 bottom-up centroid is the w-weighted mean).
  * ell (per neuron, NAN for excluded sources), dsigma and the position
- * gradients gx, gy, gz are optional outputs; returns L (NAN when M = 0). */
+ * gradients gx, gy, gz are optional outputs; returns L (NAN when M = 0).
+ * Optional OpenMP over the independent sources (threads). */
 /* ------------------------------------------------------------------------- */
 static int root_frontier(const OTree *T, int32_t i, double sigma, double theta, Frontier *F,
                          double *a, double *S_out)
@@ -1012,34 +1013,45 @@ static int root_frontier(const OTree *T, int32_t i, double sigma, double theta, 
 
 double orc_mean_length(void *t, double sigma, double theta, const int32_t *vac_ax,
                        const int32_t *vac_de, double *ell, double *dsigma, double *gx,
-                       double *gy, double *gz)
+                       double *gy, double *gz, int threads)
 {
     const OTree *T = (const OTree *)t;
     const int64_t n = T->n;
-    double *a = (double *)malloc((size_t)(n + 1) * 2 * sizeof(double));
     double *lsrc = (double *)malloc((size_t)(n ? n : 1) * sizeof(double));
-    Frontier F = {0};
     double M = 0.0, sum = 0.0, sdsig = 0.0;
-    /* pass 1: l_i and dl_i/dsigma */
-    for (int64_t i = 0; i < n; ++i) {
-        lsrc[i] = NAN;
-        if (vac_ax[i] <= 0) continue;
-        double S;
-        root_frontier(T, (int32_t)i, sigma, theta, &F, a, &S);
-        if (!(S > 0.0)) continue;
-        double l = 0.0, Db = 0.0;
-        for (int64_t k = 0; k < F.n; ++k) {
-            double q = a[k] / S;
-            l += q * sqrt(F.e[k].d2);
-            Db += q * F.e[k].d2;
+    if (threads < 1) threads = 1;
+    /* pass 1: l_i and dl_i/dsigma (sources are independent) */
+#ifdef _OPENMP
+#pragma omp parallel num_threads(threads) reduction(+ : M, sum, sdsig)
+#endif
+    {
+        double *a = (double *)malloc((size_t)(n + 1) * sizeof(double));
+        Frontier F = {0};
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+        for (int64_t i = 0; i < n; ++i) {
+            lsrc[i] = NAN;
+            if (vac_ax[i] <= 0) continue;
+            double S;
+            root_frontier(T, (int32_t)i, sigma, theta, &F, a, &S);
+            if (!(S > 0.0)) continue;
+            double l = 0.0, Db = 0.0;
+            for (int64_t k = 0; k < F.n; ++k) {
+                double q = a[k] / S;
+                l += q * sqrt(F.e[k].d2);
+                Db += q * F.e[k].d2;
+            }
+            double cov = 0.0;
+            for (int64_t k = 0; k < F.n; ++k)
+                cov += a[k] / S * (sqrt(F.e[k].d2) - l) * (F.e[k].d2 - Db);
+            lsrc[i] = l;
+            M += vac_ax[i];
+            sum += vac_ax[i] * l;
+            sdsig += vac_ax[i] * 2.0 / (sigma * sigma * sigma) * cov;
         }
-        double cov = 0.0;
-        for (int64_t k = 0; k < F.n; ++k)
-            cov += a[k] / S * (sqrt(F.e[k].d2) - l) * (F.e[k].d2 - Db);
-        lsrc[i] = l;
-        M += vac_ax[i];
-        sum += vac_ax[i] * l;
-        sdsig += vac_ax[i] * 2.0 / (sigma * sigma * sigma) * cov;
+        free(F.e);
+        free(a);
     }
     if (ell) memcpy(ell, lsrc, (size_t)n * sizeof(double));
     if (dsigma) *dsigma = M > 0 ? sdsig / M : NAN;
@@ -1047,23 +1059,39 @@ double orc_mean_length(void *t, double sigma, double theta, const int32_t *vac_a
         /* pass 2: dL/dc_k accumulated per node (G), direct terms per source */
         double *G = (double *)calloc((size_t)(T->n_nodes ? T->n_nodes : 1) * 3, sizeof(double));
         for (int64_t j = 0; j < n; ++j) gx[j] = gy[j] = gz[j] = 0.0;
-        for (int64_t i = 0; i < n && M > 0; ++i) {
-            if (!(lsrc[i] == lsrc[i])) continue; /* excluded source */
-            double S;
-            root_frontier(T, (int32_t)i, sigma, theta, &F, a, &S);
-            const double w = vac_ax[i] / M, l = lsrc[i];
-            for (int64_t k = 0; k < F.n; ++k) {
-                if (F.e[k].self || a[k] == 0.0) continue;
-                const ONode *nk = &T->nodes[F.e[k].node];
-                double r[3] = {T->px[i] - nk->cx, T->py[i] - nk->cy, T->pz[i] - nk->cz};
-                double d = sqrt(F.e[k].d2);
-                double kap = a[k] / S * (2.0 * (d - l) / (sigma * sigma) - (d > 0 ? 1.0 / d : 0.0));
-                for (int c = 0; c < 3; ++c) {
-                    double g = w * kap * r[c];
-                    G[3 * F.e[k].node + c] += g;
-                    (c == 0 ? gx : c == 1 ? gy : gz)[i] -= g;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(threads)
+#endif
+        {
+            double *a = (double *)malloc((size_t)(n + 1) * sizeof(double));
+            Frontier F = {0};
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+            for (int64_t i = 0; i < n; ++i) {
+                if (!(M > 0) || !(lsrc[i] == lsrc[i])) continue; /* excluded source */
+                double S;
+                root_frontier(T, (int32_t)i, sigma, theta, &F, a, &S);
+                const double w = vac_ax[i] / M, l = lsrc[i];
+                for (int64_t k = 0; k < F.n; ++k) {
+                    if (F.e[k].self || a[k] == 0.0) continue;
+                    const ONode *nk = &T->nodes[F.e[k].node];
+                    double r[3] = {T->px[i] - nk->cx, T->py[i] - nk->cy, T->pz[i] - nk->cz};
+                    double d = sqrt(F.e[k].d2);
+                    double kap =
+                        a[k] / S * (2.0 * (d - l) / (sigma * sigma) - (d > 0 ? 1.0 / d : 0.0));
+                    for (int c = 0; c < 3; ++c) {
+                        double g = w * kap * r[c];
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                        G[3 * F.e[k].node + c] += g;
+                        (c == 0 ? gx : c == 1 ? gy : gz)[i] -= g;
+                    }
                 }
             }
+            free(F.e);
+            free(a);
         }
         /* scatter: neuron j gets w_j * sum over the cells that hold it of G_k / N_k */
         for (int64_t v = 0; v < T->n_nodes; ++v) {
@@ -1082,8 +1110,6 @@ double orc_mean_length(void *t, double sigma, double theta, const int32_t *vac_a
         }
         free(G);
     }
-    free(F.e);
-    free(a);
     free(lsrc);
     return M > 0 ? sum / M : NAN;
 }

@@ -73,6 +73,7 @@ void free_all(relearn_ctx *c)
         (void **)&c->d_geom,     (void **)&c->d_sc,         (void **)&c->d_codes,
         (void **)&c->d_off,      (void **)&c->d_ord,        (void **)&c->d_root,
         (void **)&c->d_net,      (void **)&c->d_nkey,       (void **)&c->d_nkey_alt,
+        (void **)&c->d_lstate,   (void **)&c->d_lsum,
         (void **)&c->d_codes_alt, (void **)&c->d_perm,      (void **)&c->d_perm_alt,
         (void **)&c->d_pos,      (void **)&c->d_posq,       (void **)&c->d_mask,       (void **)&c->d_base,
         (void **)&c->d_nodes,    (void **)&c->d_parent,     (void **)&c->d_nsize,
@@ -196,6 +197,8 @@ relearn_status relearn_create_batched(relearn_ctx **out, int device, int64_t max
     A(d_off, NB + 1);
     A(d_ord, 6 * NB);
     A(d_root, NB);
+    A(d_lstate, N);
+    A(d_lsum, 4);
     if (NB > 1) {
         A(d_net, N);
         A(d_nkey, N);
@@ -325,6 +328,7 @@ relearn_status relearn_build_octree(relearn_ctx *c, int64_t n, const float *x, c
     }
     c->built = true;
     c->diag_valid = false;
+    c->length_valid = false;
     return RELEARN_OK;
 }
 
@@ -372,6 +376,7 @@ relearn_status relearn_build_octree_batch(relearn_ctx *c, int32_t num_networks,
     }
     c->built = true;
     c->diag_valid = false;
+    c->length_valid = false;
     return RELEARN_OK;
 }
 
@@ -391,6 +396,7 @@ relearn_status relearn_update_connectivity(relearn_ctx *c, const relearn_params 
     c->last_stream = st;
     const bool timed = stats || (p->flags & RELEARN_FLAG_TIMING);
     c->timed = timed;
+    c->length_valid = false;
     if (timed) CK(cudaEventRecord(c->ev[0], st), "event");
     CK(octree_reduce(c, vac_de, st), "reduce");
     if (timed) CK(cudaEventRecord(c->ev[1], st), "event");
@@ -408,6 +414,49 @@ relearn_status relearn_update_connectivity(relearn_ctx *c, const relearn_params 
     c->diag_valid = (p->flags & RELEARN_FLAG_DIAG) != 0;
     c->stats_valid = true;
     if (stats) return relearn_get_last_stats(c, stats);
+    return RELEARN_OK;
+}
+
+relearn_status relearn_mean_length(relearn_ctx *c, const relearn_params *p,
+                                   const int32_t *vac_ax, const int32_t *vac_de, float *ell,
+                                   double *mean, void *stream)
+{
+    if (!c) return RELEARN_ERR_INVALID_ARG;
+    if (!c->built) return fail(c, RELEARN_ERR_STATE, "mean_length before build_octree");
+    if (c->num_nets != 1)
+        return fail(c, RELEARN_ERR_STATE, "mean_length: needs a single-network build");
+    if (!params_ok(p)) return fail(c, RELEARN_ERR_INVALID_ARG, "mean_length: bad params");
+    if (!vac_ax || !vac_de || !mean)
+        return fail(c, RELEARN_ERR_INVALID_ARG, "mean_length: NULL argument");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(c, RELEARN_ERR_CUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    c->length_valid = false;
+    CK(octree_reduce(c, vac_de, st), "reduce");
+    CK(search_constants(c, *p, st), "constants");
+    CK(length_forward(c, vac_ax, ell, mean, st), "mean_length");
+    c->length_valid = true;
+    c->length_ran = true;
+    return RELEARN_OK;
+}
+
+relearn_status relearn_mean_length_backward(relearn_ctx *c, const int32_t *vac_ax,
+                                            const int32_t *vac_de, const double *grad_mean,
+                                            float *gx, float *gy, float *gz, double *gsigma,
+                                            void *stream)
+{
+    if (!c) return RELEARN_ERR_INVALID_ARG;
+    if (!c->length_valid)
+        return fail(c, RELEARN_ERR_STATE, "mean_length_backward without its forward");
+    if (!vac_ax || !vac_de || !gx || !gy || !gz)
+        return fail(c, RELEARN_ERR_INVALID_ARG, "mean_length_backward: NULL argument");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(c, RELEARN_ERR_CUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    c->last_stream = st;
+    CK(length_backward(c, vac_ax, vac_de, grad_mean, gx, gy, gz, gsigma, st),
+       "mean_length_backward");
     return RELEARN_OK;
 }
 
@@ -634,7 +683,8 @@ relearn_status relearn_philox4x32_10(const uint32_t *ctr, const uint32_t *key, u
 relearn_status relearn_get_last_stats(relearn_ctx *c, relearn_update_stats *stats)
 {
     if (!c || !stats) return RELEARN_ERR_INVALID_ARG;
-    if (!c->stats_valid) return fail(c, RELEARN_ERR_STATE, "no connectivity update has run");
+    if (!c->stats_valid && !c->length_ran)
+        return fail(c, RELEARN_ERR_STATE, "no connectivity update has run");
     DeviceGuard g(c->device);
     relearn_status s = sync(c);
     int64_t h[16];
@@ -648,6 +698,7 @@ relearn_status relearn_get_last_stats(relearn_ctx *c, relearn_update_stats *stat
     stats->searches_total = h[I64_Q_TOTAL];
     stats->evals_total = h[I64_EVALS_TOTAL];
     stats->walk_steps_total = h[I64_STEPS_TOTAL];
+    stats->length_evals_total = h[I64_LEN_EVALS];
     if (c->timed) {
         cudaEventElapsedTime(&stats->ms_reduce, c->ev[0], c->ev[1]);
         cudaEventElapsedTime(&stats->ms_search, c->ev[1], c->ev[3]);

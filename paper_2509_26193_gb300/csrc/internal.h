@@ -36,7 +36,8 @@ struct Geom {
 struct SearchConst {
     uint32_t thr0; // bits of (root cell length / theta)^2 (FLT_MAX for theta = 0)
     float k2;      // log2(e) / sigma^2
-    float pad[2];
+    float sigma;
+    float pad;
 };
 
 } // namespace rl
@@ -112,6 +113,10 @@ struct relearn_ctx {
     int32_t *d_need_ax = nullptr, *d_need_de = nullptr;  // [max_neurons]
     int32_t *d_keep = nullptr;                           // [max_synapses + 1]
 
+    // ---- differentiable form (expected synapse length, length.cu)
+    float4 *d_lstate = nullptr; // [n] per source (Morton position): l, Dbar, 1/S, exponent shift
+    double *d_lsum = nullptr;   // [4] sum m l, sum m (M), mean
+
     rl::ScanScratch scan;
     rl::SortScratch sort;
 
@@ -122,11 +127,13 @@ struct relearn_ctx {
     bool diag_valid = false;
     bool stats_valid = false;
     bool canonical = true; // store sorted by (src, tgt) with stable views (else rows only)
+    bool length_valid = false; // a mean-length forward ran since the last build or update
+    bool length_ran = false;   // a mean-length forward ran at least once
 };
 
 // slots of d_i64 / d_i32
 enum { I64_Q = 0, I64_FAILED, I64_DECLINED, I64_FORMED, I64_NSYN, I64_BROKEN, I64_SCAN_TOTAL,
-       I64_NODES, I64_Q_TOTAL, I64_EVALS_TOTAL, I64_ACTIVE, I64_STEPS_TOTAL };
+       I64_NODES, I64_Q_TOTAL, I64_EVALS_TOTAL, I64_ACTIVE, I64_STEPS_TOTAL, I64_LEN_EVALS };
 enum { I32_N = 0, I32_Q, I32_NSYN, I32_NEW, I32_NODES, I32_WORK, I32_ACTIVE };
 
 namespace rl {
@@ -165,6 +172,17 @@ cudaError_t search_prepare(relearn_ctx *c, const relearn_params &p, const int32_
                            cudaStream_t st);
 cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *vac_ax,
                        cudaStream_t st);
+
+// length.cu -----------------------------------------------------------------
+// Forward: per-source expected length over the root frontier and their mean.
+cudaError_t length_forward(relearn_ctx *c, const int32_t *vac_ax, float *ell, double *mean,
+                           cudaStream_t st);
+// Adjoint of the mean with respect to sigma and the positions (after length_forward).
+cudaError_t length_backward(relearn_ctx *c, const int32_t *vac_ax, const int32_t *vac_de,
+                            const double *grad_mean, float *gx, float *gy, float *gz,
+                            double *gsigma, cudaStream_t st);
+// search.cu: per-network acceptance thresholds and kernel widths from params.
+cudaError_t search_constants(relearn_ctx *c, const relearn_params &p, cudaStream_t st);
 
 // synapses.cu ---------------------------------------------------------------
 cudaError_t accept_requests(relearn_ctx *c, const relearn_params &p, const int32_t *vac_de,

@@ -67,6 +67,8 @@ __global__ void search_const_kernel(const Geom *g_all, int32_t B, float sigma, f
     sc->thr0 = __float_as_uint(fminf(thr0, 3.4028234663852886e38f));
     const double s = (double)sg;
     sc->k2 = (float)(1.4426950408889634 / (s * s));
+    sc->sigma = sg;
+    sc->pad = 0.0f;
 }
 
 // active[s] = 1 if the neuron at Morton position s has vacant axonal elements;
@@ -502,15 +504,21 @@ inline unsigned grid_for(int64_t n, int threads, int num_sms)
 
 } // namespace
 
+cudaError_t search_constants(relearn_ctx *c, const relearn_params &p, cudaStream_t st)
+{
+    search_const_kernel<<<(c->num_nets + 255) / 256, 256, 0, st>>>(
+        c->d_geom, c->num_nets, p.sigma, p.theta, p.net_sigma, p.net_theta, c->d_sc,
+        c->d_status);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t search_prepare(relearn_ctx *c, const relearn_params &p, const int32_t *vac_ax,
                            cudaStream_t st)
 {
     cudaError_t e;
     const int64_t n = c->n;
-    search_const_kernel<<<(c->num_nets + 255) / 256, 256, 0, st>>>(
-        c->d_geom, c->num_nets, p.sigma, p.theta, p.net_sigma, p.net_theta, c->d_sc,
-        c->d_status);
-    note_launch();
+    if ((e = search_constants(c, p, st))) return e;
     int32_t *active = c->d_cnt, *cnt_o = c->d_tcnt; // scratch
     query_counts_kernel<<<grid_for(n + 1, 256, c->num_sms), 256, 0, st>>>(vac_ax, c->d_perm, n,
                                                                           active, cnt_o);

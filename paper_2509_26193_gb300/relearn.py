@@ -50,7 +50,7 @@ class relearn_update_stats(ctypes.Structure):
                 ("ms_accept", ctypes.c_float), ("ms_apply", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("reserved", ctypes.c_int32),
                 ("searches_total", ctypes.c_int64), ("evals_total", ctypes.c_int64),
-                ("walk_steps_total", ctypes.c_int64)]
+                ("walk_steps_total", ctypes.c_int64), ("length_evals_total", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -70,6 +70,8 @@ _SIGS = {
     "relearn_delete_synapses": [_P, ctypes.POINTER(relearn_params), _P, _P, _P, _P,
                                 ctypes.POINTER(_I64), _P],
     "relearn_deliver_spikes": [_P, _P, _P, _P],
+    "relearn_mean_length": [_P, ctypes.POINTER(relearn_params), _P, _P, _P, _P, _P],
+    "relearn_mean_length_backward": [_P, _P, _P, _P, _P, _P, _P, _P, _P],
     "relearn_deliver_rates": [_P, _P, ctypes.c_uint64, ctypes.c_uint64, _P, _P],
     "relearn_get_synapses": [_P, _I64, ctypes.POINTER(_I64), _P, _P, _P],
     "relearn_set_synapses": [_P, _I64, _P, _P, _P],
@@ -280,6 +282,31 @@ def relearn_delete_synapses(ctx, prm, retract_ax, retract_de, vac_ax, vac_de, co
                                        ctypes.byref(b) if count else None, _stream(stream))
     _raise(ctx, st, "relearn_delete_synapses")
     return b.value if count else None
+
+
+def relearn_mean_length(ctx, prm, vac_ax, vac_de, mean, ell=None, stream=None):
+    """mean: float64 CUDA tensor (1 element), written; ell: float32 [n] or None."""
+    torch = _torch()
+    n = ctx.n
+    a = _dev_ptr(vac_ax, torch.int32, n, "vac_ax")
+    d = _dev_ptr(vac_de, torch.int32, n, "vac_de")
+    m = _dev_ptr(mean, torch.float64, 1, "mean")
+    e = None if ell is None else _dev_ptr(ell, torch.float32, n, "ell")
+    st = lib().relearn_mean_length(ctx.handle, ctypes.byref(prm), a, d, e, m, _stream(stream))
+    _raise(ctx, st, "relearn_mean_length")
+
+
+def relearn_mean_length_backward(ctx, vac_ax, vac_de, gx, gy, gz, grad_mean=None, gsigma=None,
+                                 stream=None):
+    torch = _torch()
+    n = ctx.n
+    a = _dev_ptr(vac_ax, torch.int32, n, "vac_ax")
+    d = _dev_ptr(vac_de, torch.int32, n, "vac_de")
+    g = [_dev_ptr(t, torch.float32, n, name) for t, name in ((gx, "gx"), (gy, "gy"), (gz, "gz"))]
+    gm = None if grad_mean is None else _dev_ptr(grad_mean, torch.float64, 1, "grad_mean")
+    gs = None if gsigma is None else _dev_ptr(gsigma, torch.float64, 1, "gsigma")
+    st = lib().relearn_mean_length_backward(ctx.handle, a, d, gm, *g, gs, _stream(stream))
+    _raise(ctx, st, "relearn_mean_length_backward")
 
 
 def relearn_deliver_spikes(ctx, spiked, out, stream=None):
