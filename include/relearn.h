@@ -56,10 +56,14 @@ typedef struct relearn_ctx relearn_ctx;
  *   flags     RELEARN_FLAG_* bits.
  *   search_group  tuning only (results do not depend on it): how many source neurons walk
  *             the octree together in the search kernel: 1, 8, 16 or 32 for a fixed width;
- *             0 = chosen per warp from how close its sources are (default);
+ *             2 = one source per warp, its root frontier split over the 32 lanes;
+ *             0 = chosen per warp from how close its sources are, and one source per warp
+ *             when an update has few sources (default);
  *             1000 + 100 * d32 + d8 (d32, d8 = 0..10) = chosen per warp: 32 together when
  *             they share a cell of depth >= d32, else 8 together when they share a cell of
- *             depth >= d8, else one by one.
+ *             depth >= d8, else one by one;
+ *             3000 + f (f = 0..999) = the default with one source per warp for updates of
+ *             at most f * 1024 sources.
  *   net_sigma, net_theta  device float[num_networks] or NULL (updates only): per-network
  *             sigma and theta of a batched build (relearn_build_octree_batch), replacing the
  *             scalars for network b. Values are checked on the device: a sigma that is not

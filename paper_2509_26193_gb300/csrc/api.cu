@@ -119,10 +119,11 @@ bool params_ok(const relearn_params *p)
     return p && (p->net_sigma || (p->sigma > 0.0f && p->sigma < 3.0e38f)) &&
            (p->net_theta || (p->theta >= 0.0f && p->theta < 3.0e38f)) &&
            p->step <= 0xffffffffull &&
-           (p->search_group == 0 || p->search_group == 1 || p->search_group == 8 ||
-            p->search_group == 16 || p->search_group == 32 ||
+           (p->search_group == 0 || p->search_group == 1 || p->search_group == 2 ||
+            p->search_group == 8 || p->search_group == 16 || p->search_group == 32 ||
             (p->search_group >= 1000 && p->search_group <= 2010 &&
-             (p->search_group - 1000) % 100 <= 10));
+             (p->search_group - 1000) % 100 <= 10) ||
+            (p->search_group >= 3000 && p->search_group <= 3999));
 }
 
 relearn_status read_status(relearn_ctx *c)

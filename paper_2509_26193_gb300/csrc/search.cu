@@ -44,6 +44,10 @@ constexpr float kTiny = 8.673617e-19f; // 2^-60
 // those fits such a cell, else every lane walks alone.
 constexpr int kSpreadDepth = 4;
 constexpr int kSpreadDepth8 = 4;
+// The split kernel (one warp per source) serves updates with at most kSplitWaves
+// sources per resident warp of the union kernel (a sweep on the 2^20-neuron
+// clustered network: 1 to 2 best; at 8 and more the split kernel is slower).
+constexpr int kSplitWaves = 2;
 
 // A node of depth d is accepted iff d^2 > thr0 / 4^d, thr0 = (root length / theta)^2
 // rounded to FP32 (see NodeTopo::shift). theta = 0 accepts no inner node.
@@ -153,9 +157,10 @@ struct SearchArgs {
     int32_t *diag_restarts;
     uint64_t seed;
     uint32_t step;
-    int forced_group; // 0 = choose per warp
+    int forced_group; // 0 = choose per warp; 1, 8, 16, 32 = union width; 2 = split
     int spread_depth;  // a union of 32 needs all sources in one cell this deep
     int spread_depth8; // else a union of 8 needs its sources in one cell this deep
+    int32_t split_below; // with forced_group 0: split kernel for at most this many sources
 };
 
 struct WalkOut {
@@ -265,6 +270,8 @@ template <bool kBatched>
 __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kernel(SearchArgs a)
 {
     const int32_t A = *a.d_A;
+    if (a.forced_group == 2 || (a.forced_group == 0 && A <= a.split_below))
+        return; // bh_split_kernel serves this launch
     const int lane = threadIdx.x & 31;
     int32_t root = 0, root_end = 0;
     uint32_t thr0 = 0;
@@ -493,6 +500,308 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                   (unsigned long long)my_steps);
 }
 
+// ---------------------------------------------------------------------------
+// Split kernel: one warp per source, for updates with few sources (the union
+// kernel would leave most of the GPU idle while each lane walks a whole frontier
+// alone, one dependent node load after another).
+//
+// The warp first expands the source's frontier top-down, breadth first, keeping
+// an ordered list (pre-order) of items: accepted candidates with their
+// attraction, and subtrees of rejected nodes still to be expanded. Each round
+// replaces every subtree item by its children's items (lanes in parallel, order
+// kept by a warp prefix sum) until there are at least kSplitTasks subtrees (or
+// none, or the list is full); nodes with more than 8 children (buckets) stay
+// subtrees. The lanes then walk the remaining subtrees (stackless, compensated
+// FP32 partial sums), the list's inclusive prefix is scanned in FP64 (S is its
+// total), and each lane draws one of the source's searches: the item holding
+// u * S by binary search, inside a subtree by repeating that subtree's partial
+// sum, then restarts as in the union kernel. The candidates and their order are
+// the union kernel's; only the association of the FP32/FP64 sums differs, so a
+// draw can differ from the union kernel's only within rounding of a cumulative
+// boundary.
+constexpr int kSplitCap = 128;   // items per warp
+constexpr int kSplitTasks = 48;  // stop expanding at this many subtrees
+constexpr int kSplitRounds = 12; // tree depth bound
+constexpr uint32_t kSub = 0x80000000u; // item is a subtree (node index in the low bits)
+
+struct SplitItem {
+    uint32_t node; // node index, | kSub for a subtree
+    float val;     // attraction (candidate) or partial sum (subtree, after its walk)
+};
+
+__device__ __forceinline__ int warp_excl_scan(int v, int &total)
+{
+    const int lane = threadIdx.x & 31;
+    int inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    total = __shfl_sync(0xffffffffu, inc, 31);
+    return inc - v;
+}
+
+// Restarts after the first draw picked node k (shared by nothing else: the union
+// kernel keeps its own copy inline, tuned for its registers).
+__device__ __forceinline__ int32_t split_restarts(const SearchArgs &a, int32_t k, float3 x,
+                                                  int32_t self_node, uint32_t thr0, float k2,
+                                                  int32_t i, int32_t e, int32_t &evals,
+                                                  int32_t &draws, int64_t &my_evals)
+{
+    draws = 1;
+    while (k >= 0 && draws < 24) {
+        const int4 tk = __ldg(reinterpret_cast<const int4 *>(&a.nodes[k].t));
+        if (node_is_leaf((uint32_t)tk.y)) return a.perm[tk.z];
+        const int32_t kend = tk.x;
+        float sh = 0.0f;
+        WalkOut w1 = walk<false>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2, 0.0f, 0.0f);
+        evals += w1.evals;
+        my_evals += w1.evals;
+        if (w1.sum < kTiny && w1.dmin2 < __int_as_float(0x7f800000)) {
+            sh = __fmul_rn(k2, w1.dmin2);
+            w1 = walk<false>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2, sh, 0.0f);
+        }
+        if (!(w1.sum > 0.0f)) return -1;
+        const uint32_t u = philox_x((uint32_t)i, a.step,
+                                    ((uint32_t)e << 8) | (uint32_t)depth_of((uint32_t)tk.y), 0u,
+                                    a.seed);
+        const float target = (float)((double)u * 2.3283064365386963e-10 * (double)w1.sum);
+        k = walk<true>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2, sh, target).pick;
+        ++draws;
+    }
+    return -1;
+}
+
+// A subtree item's walk: the source's candidates below node v, compensated sum
+// from zero (FIND: the first whose partial exceeds rel, else the last with weight).
+template <bool FIND>
+__device__ __forceinline__ int32_t subtree_walk(const Node *__restrict__ nodes, int32_t v,
+                                                float3 x, int32_t self_node, uint32_t thr0,
+                                                float k2, float k2sh, float rel, float &part,
+                                                float &dmin2, int32_t &evals)
+{
+    const int32_t end = __ldg(&nodes[v].t.escape);
+    int32_t p = v + 1, pick = -1;
+    float cum = 0.0f, comp = 0.0f;
+    while (p < end) {
+        const float4 g = __ldg(reinterpret_cast<const float4 *>(&nodes[p].g));
+        const int2 t = __ldg(reinterpret_cast<const int2 *>(&nodes[p].t));
+        const float d2 = dist2(x, g);
+        const bool has = g.w > 0.0f;
+        const bool acc = has && (__float_as_uint(d2) + (uint32_t)t.y > thr0);
+        if (!FIND) evals += has ? 1 : 0;
+        if (acc && p != self_node) {
+            const float at = attraction(g.w, d2, k2, k2sh);
+            kahan_add(cum, comp, at);
+            if (FIND) {
+                if (at > 0.0f) pick = p;
+                if (__fsub_rn(cum, comp) > rel) return p;
+            } else {
+                dmin2 = fminf(dmin2, d2);
+            }
+        }
+        p = (has && !acc) ? p + 1 : max(t.x, p + 1);
+    }
+    part = __fsub_rn(cum, comp);
+    return pick;
+}
+
+template <bool kBatched>
+__global__ void __launch_bounds__(256) bh_split_kernel(SearchArgs a)
+{
+    __shared__ SplitItem s_items[8][2][kSplitCap];
+    __shared__ double s_pref[8][kSplitCap];
+    const int32_t A = *a.d_A;
+    if (!(a.forced_group == 2 || (a.forced_group == 0 && A <= a.split_below))) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t my_evals = 0, my_steps = 0;
+    int32_t root = 0;
+    uint32_t thr0 = 0;
+    float k2 = 0.0f;
+    if constexpr (!kBatched) {
+        thr0 = __ldg(&a.sc->thr0);
+        k2 = __ldg(&a.sc->k2);
+    }
+    for (;;) {
+        int32_t idx = 0;
+        if (lane == 0) idx = atomicAdd(a.work, 1);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= A) break;
+        const int32_t s = a.act_src[idx];
+        const float4 xp = a.pos[s];
+        const float3 x = make_float3(xp.x, xp.y, xp.z);
+        const int32_t self_node = a.leaf_of[s];
+        if constexpr (kBatched) {
+            const int32_t net = a.net[s];
+            root = __ldg(&a.root[net]);
+            thr0 = __ldg(&a.sc[net].thr0);
+            k2 = __ldg(&a.sc[net].k2);
+        }
+        // ---- breadth-first expansion into an ordered item list
+        int cur = 0, L = 1;
+        if (lane == 0) s_items[w][0][0] = SplitItem{kSub | (uint32_t)root, 0.0f};
+        __syncwarp();
+        int32_t own = 0;
+        for (int round = 0; round < kSplitRounds; ++round) {
+            int n_sub = 0;
+            for (int b = 0; b < L; b += 32)
+                n_sub += __popc(__ballot_sync(0xffffffffu,
+                                              b + lane < L && (s_items[w][cur][b + lane].node & kSub)));
+            if (n_sub == 0 || n_sub >= kSplitTasks) break;
+            int total = 0, ev_round = 0;
+            bool over = false;
+            for (int b = 0; b < L; b += 32) {
+                const int it = b + lane;
+                SplitItem out[8];
+                int n_out = 0;
+                if (it < L) {
+                    const SplitItem item = s_items[w][cur][it];
+                    if (!(item.node & kSub)) {
+                        out[n_out++] = item;
+                    } else {
+                        const int32_t v = (int32_t)(item.node & ~kSub);
+                        const int32_t end = __ldg(&a.nodes[v].t.escape);
+                        int32_t c = v + 1, ev = 0;
+                        bool wide = false;
+                        while (c < end) {
+                            const float4 g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[c].g));
+                            const int2 t = __ldg(reinterpret_cast<const int2 *>(&a.nodes[c].t));
+                            if (g.w > 0.0f) {
+                                if (n_out == 8) { wide = true; break; }
+                                ++ev;
+                                const float d2 = dist2(x, g);
+                                if (__float_as_uint(d2) + (uint32_t)t.y > thr0) {
+                                    if (c != self_node)
+                                        out[n_out++] = SplitItem{(uint32_t)c,
+                                                                 attraction(g.w, d2, k2, 0.0f)};
+                                } else {
+                                    out[n_out++] = SplitItem{kSub | (uint32_t)c, 0.0f};
+                                }
+                            }
+                            c = max(t.x, c + 1);
+                        }
+                        if (wide) { // a bucket: keep it whole, its walk comes later
+                            n_out = 1;
+                            out[0] = item;
+                        } else {
+                            ev_round += ev;
+                        }
+                    }
+                }
+                int chunk_total;
+                const int off = total + warp_excl_scan(n_out, chunk_total);
+                if (total + chunk_total > kSplitCap) over = true;
+                else
+                    for (int q = 0; q < n_out; ++q) s_items[w][cur ^ 1][off + q] = out[q];
+                total += chunk_total;
+            }
+            __syncwarp();
+            if (over) break; // the list would overflow: walk what we have
+            for (int o = 16; o; o >>= 1) ev_round += __shfl_xor_sync(0xffffffffu, ev_round, o);
+            own += ev_round;
+            cur ^= 1;
+            L = total;
+        }
+        // ---- walk the subtrees, then the inclusive prefix (FP64) over the list
+        float k2sh = 0.0f;
+        double S = 0.0;
+        int32_t own_walk = 0;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            float dmin2 = __int_as_float(0x7f800000);
+            own_walk = 0;
+            for (int it = lane; it < L; it += 32) {
+                SplitItem item = s_items[w][cur][it];
+                const int32_t v = (int32_t)(item.node & ~kSub);
+                if (item.node & kSub) {
+                    int32_t ev = 0;
+                    subtree_walk<false>(a.nodes, v, x, self_node, thr0, k2, k2sh, 0.0f, item.val,
+                                        dmin2, ev);
+                    own_walk += ev;
+                } else {
+                    const float4 g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[v].g));
+                    const float d2 = dist2(x, g);
+                    item.val = attraction(g.w, d2, k2, k2sh);
+                    dmin2 = fminf(dmin2, d2);
+                }
+                s_items[w][cur][it].val = item.val;
+                ++my_steps;
+            }
+            __syncwarp();
+            // inclusive prefix in list order, FP64, sequential (S is its last entry)
+            if (lane == 0) {
+                double run = 0.0;
+                for (int it = 0; it < L; ++it) {
+                    run += (double)s_items[w][cur][it].val;
+                    s_pref[w][it] = run;
+                }
+            }
+            __syncwarp();
+            S = L > 0 ? s_pref[w][L - 1] : 0.0;
+            __syncwarp();
+            if (!(S < (double)kTiny)) break;
+            // every term underflowed: redo with the exponents shifted by the nearest d^2
+            for (int o = 16; o; o >>= 1) dmin2 = fminf(dmin2, __shfl_xor_sync(0xffffffffu, dmin2, o));
+            if (!(dmin2 < __int_as_float(0x7f800000))) break;
+            k2sh = __fmul_rn(k2, dmin2);
+        }
+        for (int o = 16; o; o >>= 1) own_walk += __shfl_xor_sync(0xffffffffu, own_walk, o);
+        own += own_walk;
+        if (lane == 0) my_evals += own;
+
+        // ---- draws: the source's searches, one per lane
+        const int32_t i = a.perm[s];
+        const int32_t nq = max(a.vac_ax[i], 0);
+        const int32_t qbase = a.qoff_o[i];
+        const double lns0 = S > 0.0 ? log(S) - (double)k2sh * 0.6931471805599453
+                                    : -__longlong_as_double(0x7ff0000000000000LL);
+        for (int32_t e = lane; e < nq; e += 32) {
+            int32_t result = -1, evals = own, draws = 0;
+            if (S > 0.0) {
+                const uint32_t u = philox_x((uint32_t)i, a.step, (uint32_t)e << 8, 0u, a.seed);
+                const double tgt = (double)u * 2.3283064365386963e-10 * S;
+                int lo = 0, hi = L - 1; // first item whose inclusive prefix exceeds u * S
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_pref[w][mid] > tgt)
+                        hi = mid;
+                    else
+                        lo = mid + 1;
+                }
+                const SplitItem item = s_items[w][cur][lo];
+                int32_t k = (int32_t)(item.node & ~kSub);
+                if (item.node & kSub) {
+                    const double base = lo > 0 ? s_pref[w][lo - 1] : 0.0;
+                    float part, dm;
+                    int32_t ev;
+                    k = subtree_walk<true>(a.nodes, k, x, self_node, thr0, k2, k2sh,
+                                           (float)(tgt - base), part, dm, ev);
+                }
+                result = split_restarts(a, k, x, self_node, thr0, k2, i, e, evals, draws,
+                                        my_evals);
+            }
+            const int32_t out = qbase + e;
+            a.req_tgt[out] = result;
+            if (result < 0) atomicAdd(reinterpret_cast<unsigned long long *>(a.failed), 1ull);
+            if (a.diag_lns) {
+                a.diag_lns[out] = lns0;
+                a.diag_evals[out] = evals;
+                a.diag_restarts[out] = draws > 0 ? draws - 1 : 0;
+            }
+        }
+        __syncwarp(); // the list buffers are reused by the next source
+    }
+    for (int off = 16; off; off >>= 1) {
+        my_evals += __shfl_xor_sync(0xffffffffu, my_evals, off);
+        my_steps += __shfl_xor_sync(0xffffffffu, my_steps, off);
+    }
+    if (lane == 0 && my_evals)
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.evals_total),
+                  (unsigned long long)my_evals);
+    if (lane == 0 && my_steps)
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.steps_total),
+                  (unsigned long long)my_steps);
+}
+
 inline unsigned grid_for(int64_t n, int threads, int num_sms)
 {
     int64_t b = (n + threads - 1) / threads;
@@ -570,16 +879,31 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     a.diag_restarts = diag ? c->d_diag_restarts : nullptr;
     a.seed = p.seed;
     a.step = (uint32_t)p.step;
-    // search_group: 0 = per-warp choice, 1/8/16/32 = fixed width,
-    // 1000 + 100 * d32 + d8 = per-warp choice with spread depths d32, d8 (tuning)
-    a.forced_group = p.search_group < 1000 ? (int)p.search_group : 0;
-    a.spread_depth = p.search_group >= 1000 ? (int)((p.search_group - 1000) / 100) : kSpreadDepth;
-    a.spread_depth8 = p.search_group >= 1000 ? (int)((p.search_group - 1000) % 100) : kSpreadDepth8;
+    // search_group: 0 = per-warp choice, 1/8/16/32 = fixed width, 2 = split kernel,
+    // 1000 + 100 * d32 + d8 = per-warp choice with spread depths d32, d8 (tuning),
+    // 3000 + f = per-warp choice, split kernel for at most f * 1024 sources (tuning)
+    const uint32_t sg = p.search_group;
+    a.forced_group = sg < 1000 ? (int)sg : 0;
+    const bool depths = sg >= 1000 && sg < 3000;
+    a.spread_depth = depths ? (int)((sg - 1000) / 100) : kSpreadDepth;
+    a.spread_depth8 = depths ? (int)((sg - 1000) % 100) : kSpreadDepth8;
     void (*kern)(SearchArgs) = a.net ? bh_search_kernel<true> : bh_search_kernel<false>;
-    int per_sm = 0;
+    void (*split)(SearchArgs) = a.net ? bh_split_kernel<true> : bh_split_kernel<false>;
+    int per_sm = 0, per_sm_split = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0))) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_split, split, 256, 0)))
+        return e;
     if (per_sm < 1) per_sm = 1;
+    if (per_sm_split < 1) per_sm_split = 1;
+    // the union kernel serves 32 sources per warp; below kSplitWaves sources per
+    // resident warp it would leave the GPU mostly idle
+    const int64_t warps = (int64_t)c->num_sms * per_sm * 8;
+    a.split_below = sg >= 3000 ? (int32_t)std::min<int64_t>((int64_t)(sg - 3000) * 1024, 1 << 30)
+                               : (int32_t)std::min<int64_t>(warps * kSplitWaves, 1 << 30);
+    // exactly one of the two kernels does the work (each reads the source count)
     kern<<<c->num_sms * per_sm, 256, 0, st>>>(a);
+    note_launch();
+    split<<<c->num_sms * per_sm_split, 256, 0, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }
