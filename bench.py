@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--group", type=int, default=0,
                     help="source neurons per octree walk in the search kernel (0 = default)")
     ap.add_argument("--workload", choices=["clusters", "batch", "diff"], default="clusters")
+    ap.add_argument("--regroup", action="store_true",
+                    help="two-phase search: restarts regrouped by subtree (RELEARN_FLAG_REGROUP)")
     ap.add_argument("--networks", type=int, default=256)
     return ap.parse_args()
 
@@ -186,12 +188,13 @@ class ClockSampler:
 
 # ------------------------------------------------------------------- our arm
 class Runner:
-    def __init__(self, net, theta, device, group=0):
+    def __init__(self, net, theta, device, group=0, extra_flags=0):
         import torch
         from paper_2509_26193_gb300 import build, relearn as R, workloads
         build.build()
         self.torch, self.R, self.net, self.theta = torch, R, net, theta
         self.group = group
+        self.extra_flags = extra_flags
         self.dev = device
         n = net.n
         d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
@@ -238,8 +241,8 @@ class Runner:
         R.relearn_build_octree(self.ctx, self.x, self.y, self.z)
         base = 1000 * self.step_index
         for u in range(UPDATES_PER_STEP):
-            p = R.params(self.net.sigma, self.theta, self.net.seed, base + u, R.FLAG_TIMING,
-                         self.group)
+            p = R.params(self.net.sigma, self.theta, self.net.seed, base + u,
+                         R.FLAG_TIMING | self.extra_flags, self.group)
             R.relearn_update_connectivity(self.ctx, p, self.vac_ax, self.vac_de, self.type)
             R.relearn_deliver_spikes(self.ctx, self.spiked[u], self.input)
         p = R.params(self.net.sigma, self.theta, self.net.seed, base + 999)
@@ -287,7 +290,8 @@ def first_update_profile(runner):
     runner.vac_ax.copy_(runner.vac_ax0)
     runner.vac_de.copy_(runner.vac_de0)
     R.relearn_build_octree(runner.ctx, runner.x, runner.y, runner.z)
-    p = R.params(runner.net.sigma, runner.theta, runner.net.seed, 0, 0, runner.group)
+    p = R.params(runner.net.sigma, runner.theta, runner.net.seed, 0, runner.extra_flags,
+                 runner.group)
     s = R.relearn_update_connectivity(runner.ctx, p, runner.vac_ax, runner.vac_de, runner.type,
                                       stats=True)
     p = R.params(runner.net.sigma, runner.theta, runner.net.seed, 999)
@@ -377,7 +381,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(net, args.theta)  # before any CUDA context-heavy work
-    run = Runner(net, args.theta, device, args.group)
+    from paper_2509_26193_gb300 import relearn as R
+    run = Runner(net, args.theta, device, args.group, R.FLAG_REGROUP if args.regroup else 0)
     prof = first_update_profile(run)
     for _ in range(max(args.warmup, 3)):
         run.step()
@@ -436,6 +441,7 @@ def run_ours(args):
                                  "searches_per_s": prof["searches"] / (prof["ms_total"] / 1e3)},
                 "evals_per_search": res["evals"] / max(res["searches"], 1),
                 "search_group": args.group or "default",
+                "restarts": "regrouped by subtree" if args.regroup else "inline",
                 "walk_steps_per_search": res["walk_steps"] / max(res["searches"], 1)}),
             "clocks": clk, "e2e": e2e, "gpu_launches": res["launches"],
             "roofline": roof, "cpu_baseline": cpu}

@@ -87,6 +87,11 @@ typedef struct {
  * synchronisation); read them later with relearn_get_last_stats and
  * relearn_collect_search_times. */
 #define RELEARN_FLAG_TIMING 2u
+/* Two-phase search: a search whose first draw (on the root frontier) is an inner node is
+ * queued; the queue is sorted by that node (pre-order = subtree order) and finished by a
+ * separate kernel in which neighbouring threads restart inside the same subtree. Results
+ * are bit-identical to the default (restarts finished inline by the lane that drew). */
+#define RELEARN_FLAG_REGROUP 4u
 
 /* Host-side summary of one update (filled when a stats pointer is passed; this
  * synchronises the stream). Times are CUDA-event milliseconds. */

@@ -74,6 +74,8 @@ void free_all(relearn_ctx *c)
         (void **)&c->d_off,      (void **)&c->d_ord,        (void **)&c->d_root,
         (void **)&c->d_net,      (void **)&c->d_nkey,       (void **)&c->d_nkey_alt,
         (void **)&c->d_lstate,   (void **)&c->d_lsum,
+        (void **)&c->d_rq_key,   (void **)&c->d_rq_key_alt, (void **)&c->d_rq_val,
+        (void **)&c->d_rq_val_alt, (void **)&c->d_rq_out,   (void **)&c->d_rq_src,
         (void **)&c->d_codes_alt, (void **)&c->d_perm,      (void **)&c->d_perm_alt,
         (void **)&c->d_pos,      (void **)&c->d_posq,       (void **)&c->d_mask,       (void **)&c->d_base,
         (void **)&c->d_nodes,    (void **)&c->d_parent,     (void **)&c->d_nsize,
@@ -232,6 +234,12 @@ relearn_status relearn_create_batched(relearn_ctx **out, int device, int64_t max
     A(d_toff, N + 1);
     A(d_tfill, N + 1);
     A(d_newpos, QC + 1);
+    A(d_rq_key, QC);
+    A(d_rq_key_alt, QC);
+    A(d_rq_val, QC);
+    A(d_rq_val_alt, QC);
+    A(d_rq_out, QC);
+    A(d_rq_src, QC);
     A(d_diag_lns, QC);
     A(d_diag_evals, QC);
     A(d_diag_restarts, QC);
@@ -256,7 +264,7 @@ relearn_status relearn_create_batched(relearn_ctx **out, int device, int64_t max
     A(d_need_ax, N);
     A(d_need_de, N);
     A(d_keep, S + 1);
-    const int64_t sort_blocks = sort_blocks_needed(std::max(N, S));
+    const int64_t sort_blocks = sort_blocks_needed(std::max({N, S, QC}));
     A(sort.hist, 256 * sort_blocks);
     int64_t scan_blocks = std::max({scan_blocks_needed(N + 1), scan_blocks_needed(QC),
                                     scan_blocks_needed(S), scan_blocks_needed(256 * sort_blocks)});

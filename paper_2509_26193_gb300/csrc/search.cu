@@ -30,6 +30,8 @@
 // Attraction a = count * 2^(-k2 d^2 + k2sh), k2 = log2(e) / sigma^2. k2sh = 0
 // unless every term would underflow, in which case the pass is redone with the
 // exponents shifted by the nearest candidate's d^2 (an exact common factor).
+#include <cooperative_groups.h>
+
 #include "internal.h"
 
 namespace rl {
@@ -161,6 +163,15 @@ struct SearchArgs {
     int spread_depth;  // a union of 32 needs all sources in one cell this deep
     int spread_depth8; // else a union of 8 needs its sources in one cell this deep
     int32_t split_below; // with forced_group 0: split kernel for at most this many sources
+    // deferred restarts (RELEARN_FLAG_REGROUP): searches whose first draw is an inner
+    // node are queued here and finished after a sort by that node (subtree order)
+    int defer;
+    const int32_t *req_elem;
+    uint32_t *rq_key; // drawn node
+    int32_t *rq_val;  // queue slot
+    int32_t *rq_out;  // [slot] request index
+    int32_t *rq_src;  // [slot] Morton position of the source
+    int32_t *rq_count;
 };
 
 struct WalkOut {
@@ -254,6 +265,59 @@ __device__ __forceinline__ int32_t find_root(const Node *__restrict__ nodes, int
         p = (has && !acc) ? p + 1 : max(t.x, p + 1);
     }
     return pick;
+}
+
+// Restarts after the first draw picked node k: while the drawn node is inner, its
+// frontier is walked by this lane (sum, then find), until a leaf is drawn.
+// Returns the target neuron (-1: failed); evals and draws count the work.
+__device__ __forceinline__ int32_t restart_chain(const SearchArgs &a, int32_t k, float3 x,
+                                                  int32_t self_node, uint32_t thr0, float k2,
+                                                  int32_t i, int32_t e, int32_t &evals,
+                                                  int32_t &draws, int64_t &my_evals)
+{
+    draws = 1;
+    while (k >= 0 && draws < 24) {
+        const int4 tk = __ldg(reinterpret_cast<const int4 *>(&a.nodes[k].t));
+        if (node_is_leaf((uint32_t)tk.y)) return a.perm[tk.z];
+        const int32_t kend = tk.x;
+        float sh = 0.0f;
+        WalkOut w1 = walk<false>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2, 0.0f, 0.0f);
+        evals += w1.evals;
+        my_evals += w1.evals;
+        if (w1.sum < kTiny && w1.dmin2 < __int_as_float(0x7f800000)) {
+            sh = __fmul_rn(k2, w1.dmin2);
+            w1 = walk<false>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2, sh, 0.0f);
+        }
+        if (!(w1.sum > 0.0f)) return -1;
+        const uint32_t u = philox_x((uint32_t)i, a.step,
+                                    ((uint32_t)e << 8) | (uint32_t)depth_of((uint32_t)tk.y), 0u,
+                                    a.seed);
+        const float target = (float)((double)u * 2.3283064365386963e-10 * (double)w1.sum);
+        k = walk<true>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2, sh, target).pick;
+        ++draws;
+    }
+    return -1;
+}
+
+// Deferred restart: queue search `out` of the source at Morton position s with
+// its first draw k (warp-aggregated slot allocation).
+__device__ __forceinline__ void enqueue_restart(const SearchArgs &a, int32_t k, int32_t out,
+                                                int32_t s, double lns0, int32_t evals)
+{
+    namespace cg = cooperative_groups;
+    cg::coalesced_group g = cg::coalesced_threads();
+    int32_t base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(a.rq_count, (int32_t)g.size());
+    base = g.shfl(base, 0);
+    const int32_t slot = base + (int32_t)g.thread_rank();
+    a.rq_key[slot] = (uint32_t)k;
+    a.rq_val[slot] = slot;
+    a.rq_out[slot] = out;
+    a.rq_src[slot] = s;
+    if (a.diag_lns) {
+        a.diag_lns[out] = lns0;
+        a.diag_evals[out] = evals;
+    }
 }
 
 // G = lanes per union walk (1, 8, 16 or 32), chosen per warp task from the spread of
@@ -445,38 +509,12 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                 if (k < 0) // u * S rounded up to S past the last weighted candidate
                     k = find_root(a.nodes, root + 1, root_end, 0.0f, 0.0f, x, self_node, thr0,
                                   k2, k2sh, __int_as_float(0x7f800000));
-                draws = 1;
-                while (k >= 0 && draws < 24) {
-                    const int4 tk = __ldg(reinterpret_cast<const int4 *>(&a.nodes[k].t));
-                    if (node_is_leaf((uint32_t)tk.y)) {
-                        result = a.perm[tk.z];
-                        break;
-                    }
-                    // restart at the drawn inner node: its frontier is walked per lane
-                    const int32_t kend = tk.x;
-                    float sh = 0.0f;
-                    WalkOut w1 = walk<false>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2,
-                                             0.0f, 0.0f);
-                    evals += w1.evals;
-                    my_evals += w1.evals;
-                    if (w1.sum < kTiny && w1.dmin2 < __int_as_float(0x7f800000)) {
-                        sh = __fmul_rn(k2, w1.dmin2);
-                        w1 = walk<false>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2, sh,
-                                         0.0f);
-                    }
-                    if (!(w1.sum > 0.0f)) {
-                        k = -1;
-                        break;
-                    }
-                    u = philox_x((uint32_t)i, a.step,
-                                 ((uint32_t)e << 8) | (uint32_t)depth_of((uint32_t)tk.y), 0u,
-                                 a.seed);
-                    const float target =
-                        (float)((double)u * 2.3283064365386963e-10 * (double)w1.sum);
-                    k = walk<true>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2, sh, target)
-                            .pick;
-                    ++draws;
+                if (a.defer && k >= 0 &&
+                    !node_is_leaf((uint32_t)__ldg(&a.nodes[k].t.shift))) {
+                    enqueue_restart(a, k, qbase + e, s, lns0, evals);
+                    continue; // finished by bh_restart_kernel
                 }
+                result = restart_chain(a, k, x, self_node, thr0, k2, i, e, evals, draws, my_evals);
             }
             const int32_t out = qbase + e;
             a.req_tgt[out] = result;
@@ -539,37 +577,6 @@ __device__ __forceinline__ int warp_excl_scan(int v, int &total)
     }
     total = __shfl_sync(0xffffffffu, inc, 31);
     return inc - v;
-}
-
-// Restarts after the first draw picked node k (shared by nothing else: the union
-// kernel keeps its own copy inline, tuned for its registers).
-__device__ __forceinline__ int32_t split_restarts(const SearchArgs &a, int32_t k, float3 x,
-                                                  int32_t self_node, uint32_t thr0, float k2,
-                                                  int32_t i, int32_t e, int32_t &evals,
-                                                  int32_t &draws, int64_t &my_evals)
-{
-    draws = 1;
-    while (k >= 0 && draws < 24) {
-        const int4 tk = __ldg(reinterpret_cast<const int4 *>(&a.nodes[k].t));
-        if (node_is_leaf((uint32_t)tk.y)) return a.perm[tk.z];
-        const int32_t kend = tk.x;
-        float sh = 0.0f;
-        WalkOut w1 = walk<false>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2, 0.0f, 0.0f);
-        evals += w1.evals;
-        my_evals += w1.evals;
-        if (w1.sum < kTiny && w1.dmin2 < __int_as_float(0x7f800000)) {
-            sh = __fmul_rn(k2, w1.dmin2);
-            w1 = walk<false>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2, sh, 0.0f);
-        }
-        if (!(w1.sum > 0.0f)) return -1;
-        const uint32_t u = philox_x((uint32_t)i, a.step,
-                                    ((uint32_t)e << 8) | (uint32_t)depth_of((uint32_t)tk.y), 0u,
-                                    a.seed);
-        const float target = (float)((double)u * 2.3283064365386963e-10 * (double)w1.sum);
-        k = walk<true>(a.nodes, k + 1, kend, 0.0f, x, self_node, thr0, k2, sh, target).pick;
-        ++draws;
-    }
-    return -1;
 }
 
 // A subtree item's walk: the source's candidates below node v, compensated sum
@@ -776,8 +783,8 @@ __global__ void __launch_bounds__(256) bh_split_kernel(SearchArgs a)
                     k = subtree_walk<true>(a.nodes, k, x, self_node, thr0, k2, k2sh,
                                            (float)(tgt - base), part, dm, ev);
                 }
-                result = split_restarts(a, k, x, self_node, thr0, k2, i, e, evals, draws,
-                                        my_evals);
+                result = restart_chain(a, k, x, self_node, thr0, k2, i, e, evals, draws,
+                                       my_evals);
             }
             const int32_t out = qbase + e;
             a.req_tgt[out] = result;
@@ -800,6 +807,49 @@ __global__ void __launch_bounds__(256) bh_split_kernel(SearchArgs a)
     if (lane == 0 && my_steps)
         atomicAdd(reinterpret_cast<unsigned long long *>(a.steps_total),
                   (unsigned long long)my_steps);
+}
+
+// Deferred restarts, one thread per queued search, in the order of their drawn
+// node (pre-order, so neighbouring threads walk the same subtree and share its
+// nodes in L1). The arithmetic is restart_chain's: results equal the inline path.
+template <bool kBatched>
+__global__ void __launch_bounds__(256) bh_restart_kernel(SearchArgs a, const uint32_t *keys,
+                                                         const int32_t *vals)
+{
+    const int32_t P = *a.rq_count;
+    int64_t my_evals = 0;
+    uint32_t thr0 = 0;
+    float k2 = 0.0f;
+    if constexpr (!kBatched) {
+        thr0 = __ldg(&a.sc->thr0);
+        k2 = __ldg(&a.sc->k2);
+    }
+    for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < P; j += gridDim.x * blockDim.x) {
+        const int32_t slot = vals[j];
+        const int32_t k = (int32_t)keys[j];
+        const int32_t out = a.rq_out[slot], s = a.rq_src[slot];
+        const int32_t i = a.perm[s], e = a.req_elem[out];
+        const float4 xp = a.pos[s];
+        const float3 x = make_float3(xp.x, xp.y, xp.z);
+        if constexpr (kBatched) {
+            const int32_t net = a.net[s];
+            thr0 = __ldg(&a.sc[net].thr0);
+            k2 = __ldg(&a.sc[net].k2);
+        }
+        int32_t evals = a.diag_evals ? a.diag_evals[out] : 0, draws = 0;
+        const int32_t result =
+            restart_chain(a, k, x, a.leaf_of[s], thr0, k2, i, e, evals, draws, my_evals);
+        a.req_tgt[out] = result;
+        if (result < 0) atomicAdd(reinterpret_cast<unsigned long long *>(a.failed), 1ull);
+        if (a.diag_lns) {
+            a.diag_evals[out] = evals;
+            a.diag_restarts[out] = draws > 0 ? draws - 1 : 0;
+        }
+    }
+    for (int off = 16; off; off >>= 1) my_evals += __shfl_xor_sync(0xffffffffu, my_evals, off);
+    if ((threadIdx.x & 31) == 0 && my_evals)
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.evals_total),
+                  (unsigned long long)my_evals);
 }
 
 inline unsigned grid_for(int64_t n, int threads, int num_sms)
@@ -879,6 +929,14 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     a.diag_restarts = diag ? c->d_diag_restarts : nullptr;
     a.seed = p.seed;
     a.step = (uint32_t)p.step;
+    a.defer = (p.flags & RELEARN_FLAG_REGROUP) != 0;
+    a.req_elem = c->d_req_elem;
+    a.rq_key = c->d_rq_key;
+    a.rq_val = c->d_rq_val;
+    a.rq_out = c->d_rq_out;
+    a.rq_src = c->d_rq_src;
+    a.rq_count = c->d_i32 + I32_RQ;
+    if (a.defer && (e = cudaMemsetAsync(a.rq_count, 0, sizeof(int32_t), st))) return e;
     // search_group: 0 = per-warp choice, 1/8/16/32 = fixed width, 2 = split kernel,
     // 1000 + 100 * d32 + d8 = per-warp choice with spread depths d32, d8 (tuning),
     // 3000 + f = per-warp choice, split kernel for at most f * 1024 sources (tuning)
@@ -905,6 +963,22 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     note_launch();
     split<<<c->num_sms * per_sm_split, 256, 0, st>>>(a);
     note_launch();
+    if (a.defer) {
+        // regroup the deferred restarts by drawn node, then finish them
+        int bits = 1;
+        while (bits < 32 && ((int64_t)1 << bits) <= c->max_nodes) ++bits;
+        int which = 0;
+        if ((e = radix_sort_u32(c->d_rq_key, c->d_rq_key_alt, c->d_rq_val, c->d_rq_val_alt,
+                                c->max_searches, a.rq_count, bits, c->sort, st, &which)))
+            return e;
+        void (*rk)(SearchArgs, const uint32_t *, const int32_t *) =
+            a.net ? bh_restart_kernel<true> : bh_restart_kernel<false>;
+        int per_sm_rk = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_rk, rk, 256, 0))) return e;
+        rk<<<c->num_sms * (per_sm_rk > 0 ? per_sm_rk : 1), 256, 0, st>>>(
+            a, which ? c->d_rq_key_alt : c->d_rq_key, which ? c->d_rq_val_alt : c->d_rq_val);
+        note_launch();
+    }
     return cudaGetLastError();
 }
 

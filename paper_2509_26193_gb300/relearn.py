@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CAPACITY", 5
                 6: "STATE"}
 FLAG_DIAG = 1
 FLAG_TIMING = 2
+FLAG_REGROUP = 4
 
 _lock = threading.Lock()
 _lib = None

@@ -161,6 +161,32 @@ def test_results_do_not_depend_on_search_group():
     assert np.array_equal(uev[same], sev[same])
 
 
+def test_regrouped_restarts_are_bit_identical():
+    """Two-phase search (restarts queued, sorted by their subtree, finished by a
+    separate kernel) gives exactly the requests, diagnostics and acceptances of the
+    inline path, for the union kernel and on a multi-update run."""
+    from paper_2509_26193_gb300 import relearn as R
+    net = workloads.gaussian_clusters(n=40000, clusters=6, side=3000, std=150, seed=34,
+                                      sigma=300.0)
+    runs = []
+    for flags in (R.FLAG_DIAG, R.FLAG_DIAG | R.FLAG_REGROUP):
+        g = GpuNet(net)
+        rows = []
+        for step in range(3):
+            p = R.params(net.sigma, net.theta, net.seed, step, flags, 3000)
+            st = R.relearn_update_connectivity(g.ctx, p, g.vac_ax, g.vac_de, g.type,
+                                               stats=True)
+            tgt, acc = g.requests()
+            dg = R.relearn_get_search_diag(g.ctx)
+            rows.append((tgt, acc, dg["ln_s0"], dg["evals"], dg["restarts"], st["failed"],
+                         st["formed"], st["evals_total"]))
+        runs.append(rows)
+        g.close()
+    for r0, r1 in zip(*runs):
+        for a, b in zip(r0, r1):
+            assert np.array_equal(a, b)
+
+
 def test_accept_apply_match_oracle_replay():
     net = workloads.gaussian_clusters(n=30000, clusters=5, side=2500, std=150, seed=51,
                                       sigma=300.0)
