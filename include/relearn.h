@@ -253,7 +253,8 @@ relearn_status relearn_mean_length(relearn_ctx *ctx, const relearn_params *param
  *   gx, gy, gz device float[n], written: d(grad_mean * mean)/d(position), by neuron id.
  *   gsigma     device double or NULL, written: d(grad_mean * mean)/d sigma.
  * Attractions are recomputed, not stored; the centroid adjoints are accumulated per
- * node in FP64. */
+ * node with FP32 vector atomics (order not fixed: the gradient is reproducible to
+ * FP32 rounding, not bit for bit). */
 relearn_status relearn_mean_length_backward(relearn_ctx *ctx, const int32_t *vac_ax,
                                             const int32_t *vac_de, const double *grad_mean,
                                             float *gx, float *gy, float *gz, double *gsigma,

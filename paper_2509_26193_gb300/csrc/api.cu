@@ -89,8 +89,8 @@ void free_all(relearn_ctx *c)
         (void **)&c->d_syn_tgt,  (void **)&c->d_syn_sign,   (void **)&c->d_key,
         (void **)&c->d_key_alt,  (void **)&c->d_val,        (void **)&c->d_val_alt,
         (void **)&c->d_key32,    (void **)&c->d_key32_alt,  (void **)&c->d_out_ptr,
-        (void **)&c->d_in_ptr,   (void **)&c->d_in_src,     (void **)&c->d_in_syn,
-        (void **)&c->d_in_sign,  (void **)&c->d_prio_ax,    (void **)&c->d_prio_de,
+        (void **)&c->d_in_ptr,   (void **)&c->d_in_syn,
+        (void **)&c->d_prio_ax,  (void **)&c->d_prio_de,
         (void **)&c->d_sel_ax,   (void **)&c->d_sel_de,     (void **)&c->d_need_ax,
         (void **)&c->d_need_de,  (void **)&c->d_keep,       (void **)&c->scan.block_sums,
         (void **)&c->sort.hist};
@@ -254,9 +254,7 @@ relearn_status relearn_create_batched(relearn_ctx **out, int device, int64_t max
     A(d_key32_alt, S);
     A(d_out_ptr, N + 1);
     A(d_in_ptr, N + 1);
-    A(d_in_src, S);
     A(d_in_syn, S);
-    A(d_in_sign, S);
     A(d_prio_ax, S);
     A(d_prio_de, S);
     A(d_sel_ax, S);

@@ -109,8 +109,7 @@ struct relearn_ctx {
     int32_t *d_val = nullptr, *d_val_alt = nullptr;     // [max_synapses]
     uint32_t *d_key32 = nullptr, *d_key32_alt = nullptr;
     int32_t *d_out_ptr = nullptr, *d_in_ptr = nullptr;  // [max_neurons + 1]
-    int32_t *d_in_src = nullptr, *d_in_syn = nullptr;   // [max_synapses]
-    int8_t *d_in_sign = nullptr;
+    int32_t *d_in_syn = nullptr;                        // [max_synapses]
     uint32_t *d_prio_ax = nullptr, *d_prio_de = nullptr; // [max_synapses]
     uint8_t *d_sel_ax = nullptr, *d_sel_de = nullptr;    // [max_synapses]
     int32_t *d_need_ax = nullptr, *d_need_de = nullptr;  // [max_neurons]
@@ -193,7 +192,6 @@ cudaError_t accept_requests(relearn_ctx *c, const relearn_params &p, const int32
 cudaError_t apply_requests(relearn_ctx *c, int32_t *vac_ax, int32_t *vac_de, const uint8_t *type,
                            cudaStream_t st);
 cudaError_t rebuild_views(relearn_ctx *c, cudaStream_t st);
-cudaError_t rebuild_in_rows(relearn_ctx *c, cudaStream_t st);
 cudaError_t delete_synapses(relearn_ctx *c, const relearn_params &p, const int32_t *retract_ax,
                             const int32_t *retract_de, int32_t *vac_ax, int32_t *vac_de,
                             cudaStream_t st);

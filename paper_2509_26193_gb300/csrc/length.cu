@@ -16,10 +16,13 @@
 // FP32 attractions with Kahan-compensated sums; S, l and Dbar formed in FP64 and
 // kept per source with the exponent shift. Backward: the same walk again,
 // recomputing every attraction (nothing per candidate is stored), accumulating
-// the centroid adjoints G_k = sum_i (m_i / M) dl_i/dc_k per node (warp-reduced,
-// one FP64 atomic per node and warp step) and each source's direct term in
-// registers; then every neuron j adds w_j * sum over its cells k of G_k / N_k
-// (its leaf's parent chain).
+// the centroid adjoints G_k = sum_i (m_i / M) dl_i/dc_k per node (one 16-byte
+// vector atomic add per lane and candidate: all lanes of a union walk add to the
+// same node in one instruction, which the memory system combines; measured 1.65x
+// faster than a warp shuffle reduction followed by FP64 atomics, with a gradient
+// norm error of 1.6e-5 instead of 3e-6 against the FP64 oracle at 2^18 neurons)
+// and each source's direct term in registers; then every neuron j adds
+// w_j * sum over its cells k of G_k / N_k (its leaf's parent chain, in FP64).
 #include "internal.h"
 
 namespace rl {
@@ -53,7 +56,7 @@ struct LenArgs {
     double *lsum;   // [4]
     int32_t *work;
     // backward
-    double *G;           // [nodes][4] centroid adjoints
+    float4 *G;           // [nodes] centroid adjoints (x, y, z, unused)
     float *gx, *gy, *gz; // id order
     const double *gout;  // upstream gradient of the mean (NULL = 1)
     double *gsigma;
@@ -117,11 +120,9 @@ __device__ __forceinline__ void bwd_visit(Bwd &b, const Src &s, float cnt, float
     b.gz = __fsub_rn(b.gz, oz);
 }
 
-__device__ __forceinline__ void add_node(double *G, int32_t p, float ox, float oy, float oz)
+__device__ __forceinline__ void add_node(float4 *G, int32_t p, float ox, float oy, float oz)
 {
-    atomicAdd(&G[4 * (int64_t)p + 0], (double)ox);
-    atomicAdd(&G[4 * (int64_t)p + 1], (double)oy);
-    atomicAdd(&G[4 * (int64_t)p + 2], (double)oz);
+    atomicAdd(&G[p], make_float4(ox, oy, oz, 0.0f));
 }
 
 // A lane's own walk of its root frontier (stackless: expand = p + 1, accept or
@@ -221,20 +222,10 @@ __global__ void __launch_bounds__(256) length_kernel(LenArgs a)
                 if constexpr (!kBack) {
                     if (take) fwd_visit(f, g.w, D, k2, 0.0f);
                 } else {
-                    float ox = 0.f, oy = 0.f, oz = 0.f;
-                    if (take) bwd_visit(b, s, g.w, rx, ry, rz, D, k2, two_s2, ox, oy, oz);
-                    const uint32_t m = __ballot_sync(0xffffffffu, take);
-                    if (m) {
-                        if (__popc(m) > 1) { // every lane is at node p: reduce, one atomic
-                            for (int o = 16; o; o >>= 1) {
-                                ox += __shfl_xor_sync(0xffffffffu, ox, o);
-                                oy += __shfl_xor_sync(0xffffffffu, oy, o);
-                                oz += __shfl_xor_sync(0xffffffffu, oz, o);
-                            }
-                            if (lane == __ffs(m) - 1) add_node(a.G, p, ox, oy, oz);
-                        } else if (take) {
-                            add_node(a.G, p, ox, oy, oz);
-                        }
+                    if (take) {
+                        float ox, oy, oz;
+                        bwd_visit(b, s, g.w, rx, ry, rz, D, k2, two_s2, ox, oy, oz);
+                        add_node(a.G, p, ox, oy, oz);
                     }
                 }
                 p = __any_sync(0xffffffffu, on && !pass) ? p + 1 : max(t.x, p + 1);
@@ -333,12 +324,12 @@ __global__ void len_finish_kernel(const float4 *__restrict__ state,
     }
 }
 
-__global__ void zero_nodes_kernel(double *G, const int64_t *d_num_nodes)
+__global__ void zero_nodes_kernel(float4 *G, const int64_t *d_num_nodes)
 {
-    const int64_t m = 4 * *d_num_nodes;
+    const int64_t m = *d_num_nodes;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
          k += (int64_t)gridDim.x * blockDim.x)
-        G[k] = 0.0;
+        G[k] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Neuron j (Morton position s) gets w_j * sum over its cells k of G_k / N_k.
@@ -346,7 +337,7 @@ __global__ void len_scatter_kernel(const Node *__restrict__ nodes,
                                    const int32_t *__restrict__ parent,
                                    const int32_t *__restrict__ leaf_of,
                                    const int32_t *__restrict__ perm,
-                                   const int32_t *__restrict__ vac_de, const double *__restrict__ G,
+                                   const int32_t *__restrict__ vac_de, const float4 *__restrict__ G,
                                    int64_t n, float *gx, float *gy, float *gz)
 {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
@@ -359,9 +350,10 @@ __global__ void len_scatter_kernel(const Node *__restrict__ nodes,
             const int32_t cnt = nodes[u].t.icount;
             if (cnt <= 0) continue;
             const double inv = 1.0 / (double)cnt;
-            hx += G[4 * (int64_t)u + 0] * inv;
-            hy += G[4 * (int64_t)u + 1] * inv;
-            hz += G[4 * (int64_t)u + 2] * inv;
+            const float4 gu = G[u];
+            hx += (double)gu.x * inv;
+            hy += (double)gu.y * inv;
+            hz += (double)gu.z * inv;
         }
         gx[i] += (float)(w * hx);
         gy[i] += (float)(w * hy);
@@ -434,8 +426,9 @@ cudaError_t length_backward(relearn_ctx *c, const int32_t *vac_ax, const int32_t
 {
     cudaError_t e;
     const int64_t n = c->n;
-    double *G = c->d_acc; // free between bottom-up updates: 4 doubles per node
-    zero_nodes_kernel<<<grid_for(4 * c->max_nodes, 256, c->num_sms), 256, 0, st>>>(
+    // d_acc is free between bottom-up updates (32 bytes per node; 16 used here)
+    float4 *G = reinterpret_cast<float4 *>(c->d_acc);
+    zero_nodes_kernel<<<grid_for(c->max_nodes, 256, c->num_sms), 256, 0, st>>>(
         G, c->d_i64 + I64_NODES);
     note_launch();
     for (float *g : {gx, gy, gz})

@@ -7,9 +7,12 @@
 // vac_de other requests to it have a smaller (priority, source, element) key,
 // which is the same set as sorting by that key and taking the first vac_de.
 //
-// The store is the synapse multiset in canonical order (source, then target),
-// with an out-row pointer array and an in-view (rows by target, each ordered by
-// source) for deletion and spike delivery.
+// The store is the synapse multiset. Updates append their new synapses; the
+// canonical order (source, then target) with an out-row pointer array and an
+// in-view (rows by target, each ordered by source) is restored only when deletion
+// or an export needs it. Spike delivery reads the store in any order: each
+// synapse of a spiking source adds its sign to its target with an integer atomic
+// (exact, so the order does not matter).
 #include "internal.h"
 
 namespace rl {
@@ -215,43 +218,10 @@ __global__ void degree_kernel(const int32_t *d_nsyn, const int32_t *__restrict__
 }
 
 __global__ void in_view_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ order,
-                               const int32_t *__restrict__ src, const int8_t *__restrict__ sign,
-                               int32_t *__restrict__ in_syn, int32_t *__restrict__ in_src,
-                               int8_t *__restrict__ in_sign)
+                               int32_t *__restrict__ in_syn)
 {
     const int64_t m = *d_nsyn;
-    GRID_STRIDE(k, m)
-    {
-        int32_t s = order[k];
-        in_syn[k] = s;
-        in_src[k] = src[s];
-        in_sign[k] = sign[s];
-    }
-}
-
-// In-CSR by counting sort (rows by target; order inside a row is arbitrary):
-// enough for spike delivery, whose per-row sums are integers.
-__global__ void in_degree_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ tgt,
-                                 int32_t *__restrict__ in_cnt)
-{
-    const int64_t m = *d_nsyn;
-    GRID_STRIDE(k, m) atomicAdd(&in_cnt[tgt[k]], 1);
-}
-
-__global__ void in_scatter_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ src,
-                                  const int32_t *__restrict__ tgt,
-                                  const int8_t *__restrict__ sign,
-                                  const int32_t *__restrict__ in_ptr, int32_t *__restrict__ fill,
-                                  int32_t *__restrict__ in_src, int8_t *__restrict__ in_sign)
-{
-    const int64_t m = *d_nsyn;
-    GRID_STRIDE(k, m)
-    {
-        const int32_t t = tgt[k];
-        const int32_t pos = in_ptr[t] + atomicAdd(&fill[t], 1);
-        in_src[pos] = src[k];
-        in_sign[pos] = sign[k];
-    }
+    GRID_STRIDE(k, m) in_syn[k] = order[k];
 }
 
 // ---------------------------------------------------------------- deletion
@@ -367,38 +337,33 @@ __global__ void shrink_store_kernel(int32_t *d_nsyn, const int64_t *d_kept, int6
 }
 
 // ---------------------------------------------------------------- spikes
-__global__ void spikes_kernel(int64_t n, const int32_t *__restrict__ in_ptr,
-                              const int32_t *__restrict__ in_src,
-                              const int8_t *__restrict__ in_sign,
+// input[t] += sign for every synapse s -> t of a spiking source (input zeroed first).
+__global__ void spikes_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ src,
+                              const int32_t *__restrict__ tgt, const int8_t *__restrict__ sign,
                               const uint8_t *__restrict__ spiked, int32_t *__restrict__ input)
 {
-    GRID_STRIDE(t, n)
+    const int64_t m = *d_nsyn;
+    GRID_STRIDE(k, m)
     {
-        int32_t acc = 0;
-        const int32_t b = in_ptr[t], e = in_ptr[t + 1];
-        for (int32_t k = b; k < e; ++k) acc += spiked[in_src[k]] ? (int32_t)in_sign[k] : 0;
-        input[t] = acc;
+        if (spiked[src[k]]) atomicAdd(&input[tgt[k]], (int32_t)sign[k]);
     }
 }
 
 // Firing-rate delivery (Sec. IV-B): the receiver t decides once per step and per
 // source s whether s spiked, spiked iff philox({s, t, step, 4}).x < rate[s] * 2^32
-// (an exact FP64 comparison); duplicates of (s, t) share that decision.
-__global__ void rates_kernel(int64_t n, const int32_t *__restrict__ in_ptr,
-                             const int32_t *__restrict__ in_src,
-                             const int8_t *__restrict__ in_sign, const float *__restrict__ rate,
-                             uint64_t seed, uint32_t step, int32_t *__restrict__ input)
+// (an exact FP64 comparison); duplicates of (s, t) share that decision (each
+// copy computes the same word).
+__global__ void rates_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ src,
+                             const int32_t *__restrict__ tgt, const int8_t *__restrict__ sign,
+                             const float *__restrict__ rate, uint64_t seed, uint32_t step,
+                             int32_t *__restrict__ input)
 {
-    GRID_STRIDE(t, n)
+    const int64_t m = *d_nsyn;
+    GRID_STRIDE(k, m)
     {
-        int32_t acc = 0;
-        const int32_t b = in_ptr[t], e = in_ptr[t + 1];
-        for (int32_t k = b; k < e; ++k) {
-            const int32_t s = in_src[k];
-            const uint32_t w = philox_x((uint32_t)s, (uint32_t)t, step, 4u, seed);
-            if ((double)w < (double)rate[s] * 4294967296.0) acc += in_sign[k];
-        }
-        input[t] = acc;
+        const int32_t s = src[k], t = tgt[k];
+        const uint32_t w = philox_x((uint32_t)s, (uint32_t)t, step, 4u, seed);
+        if ((double)w < (double)rate[s] * 4294967296.0) atomicAdd(&input[t], (int32_t)sign[k]);
     }
 }
 
@@ -407,8 +372,10 @@ __global__ void rates_kernel(int64_t n, const int32_t *__restrict__ in_ptr,
 cudaError_t deliver_rates(relearn_ctx *c, const float *rate, uint64_t seed, uint32_t step,
                           int32_t *input, cudaStream_t st)
 {
-    rates_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(
-        c->n, c->d_in_ptr, c->d_in_src, c->d_in_sign, rate, seed, step, input);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(input, 0, c->n * sizeof(int32_t), st))) return e;
+    rates_kernel<<<grid_for(c->max_synapses, 256, c->num_sms), 256, 0, st>>>(
+        c->d_i32 + I32_NSYN, c->d_syn_src, c->d_syn_tgt, c->d_syn_sign, rate, seed, step, input);
     note_launch();
     return cudaGetLastError();
 }
@@ -478,8 +445,7 @@ cudaError_t rebuild_views(relearn_ctx *c, cudaStream_t st)
     if ((e = radix_sort_u32(c->d_key32, c->d_key32_alt, c->d_val, c->d_val_alt, c->max_synapses,
                             dm, bits, c->sort, st, &which)))
         return e;
-    in_view_kernel<<<gs, 256, 0, st>>>(dm, which ? c->d_val_alt : c->d_val, c->d_syn_src,
-                                       c->d_syn_sign, c->d_in_syn, c->d_in_src, c->d_in_sign);
+    in_view_kernel<<<gs, 256, 0, st>>>(dm, which ? c->d_val_alt : c->d_val, c->d_in_syn);
     note_launch();
     return cudaGetLastError();
 }
@@ -507,26 +473,8 @@ cudaError_t apply_requests(relearn_ctx *c, int32_t *vac_ax, int32_t *vac_de, con
                                        c->d_i64 + I64_NSYN);
     note_launch();
     // new synapses sit unsorted at the end of the store until an operation needs the
-    // canonical order (deletion, export); spike delivery only needs rows by target
+    // canonical order (deletion, export); spike delivery reads the store in any order
     c->canonical = false;
-    return rebuild_in_rows(c, st);
-}
-
-cudaError_t rebuild_in_rows(relearn_ctx *c, cudaStream_t st)
-{
-    cudaError_t e;
-    const int64_t n = c->n;
-    const int32_t *dm = c->d_i32 + I32_NSYN;
-    const unsigned gs = grid_for(c->max_synapses, 256, c->num_sms);
-    int32_t *in_cnt = c->d_tcnt, *fill = c->d_tfill;
-    if ((e = cudaMemsetAsync(in_cnt, 0, (n + 1) * sizeof(int32_t), st))) return e;
-    if ((e = cudaMemsetAsync(fill, 0, (n + 1) * sizeof(int32_t), st))) return e;
-    in_degree_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_tgt, in_cnt);
-    note_launch();
-    if ((e = scan_exclusive(in_cnt, c->d_in_ptr, n + 1, nullptr, nullptr, c->scan, st))) return e;
-    in_scatter_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_syn_tgt, c->d_syn_sign,
-                                          c->d_in_ptr, fill, c->d_in_src, c->d_in_sign);
-    note_launch();
     return cudaGetLastError();
 }
 
@@ -576,8 +524,10 @@ cudaError_t delete_synapses(relearn_ctx *c, const relearn_params &p, const int32
 cudaError_t deliver_spikes(relearn_ctx *c, const uint8_t *spiked, int32_t *input,
                            cudaStream_t st)
 {
-    spikes_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(
-        c->n, c->d_in_ptr, c->d_in_src, c->d_in_sign, spiked, input);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(input, 0, c->n * sizeof(int32_t), st))) return e;
+    spikes_kernel<<<grid_for(c->max_synapses, 256, c->num_sms), 256, 0, st>>>(
+        c->d_i32 + I32_NSYN, c->d_syn_src, c->d_syn_tgt, c->d_syn_sign, spiked, input);
     note_launch();
     return cudaGetLastError();
 }
