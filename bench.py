@@ -416,7 +416,8 @@ def run_ours(args):
     peak_tflops = SM_COUNT * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
     flops = FLOPS_PER_EVAL * res["evals"]
     achieved = flops / (res["kernel_ms"] / 1000.0) / 1e12 if res["kernel_ms"] > 0 else 0.0
-    roof = {"bound": "alu", "kernel": "bh_search_kernel", "achieved": achieved,
+    roof = {"bound": "alu", "kernel": "search (bh_search_kernel + bh_split_kernel, one launch "
+                                      "pair per update)", "achieved": achieved,
             "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
             "traffic": search_traffic(),
             "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop/FMA x "
