@@ -715,9 +715,6 @@ def run_diff(args):
     device = torch.device("cuda", local if ws > 1 else torch.cuda.current_device())
     torch.cuda.set_device(device)
     net = workloads.differentiable_cube()
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = diff_cpu_baseline(net)
     build.build()
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
     x, y, z = (d(a).requires_grad_(True) for a in (net.x, net.y, net.z))
@@ -789,6 +786,8 @@ def run_diff(args):
         if rank != 0:
             dist.destroy_process_group()
             return
+    # the oracle last: its OpenMP threads would compete with the host loop above
+    cpu = None if ws > 1 or args.no_cpu_baseline else diff_cpu_baseline(net)
     peak_tflops = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     flops = evals / 2 * (FLOPS_PER_CAND_FWD + FLOPS_PER_CAND_BWD)
     achieved = flops / (ms / 1000.0) / 1e12
