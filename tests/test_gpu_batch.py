@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import LNS_TOL, compare_targets, dev
+from gpu_common import AC_MARGIN, LNS_TOL, compare_targets, dev
 from paper_2509_26193_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -254,3 +254,48 @@ def test_batch_step_in_a_cuda_graph_matches_direct_calls():
     torch.cuda.synchronize()
     assert torch.equal(tgt_copy, direct)
     g2.close()
+
+
+def test_full_size_batch_sampled():
+    """The batched benchmark workload (256 networks, log-uniform 10^3 .. 10^6
+    neurons, 3.7e7 in total) in the benchmark's launch configuration (the search
+    width the autotuner picks there, 1303, and the default): sampled searches of
+    six networks (the smallest, the largest and four others) against the oracle,
+    and each sampled network's acceptance replayed exactly."""
+    from paper_2509_26193_gb300 import relearn as R
+    b = workloads.network_batch(networks=256, seed=4)
+    sizes = np.diff(b.offsets)
+    rng = np.random.default_rng(9)
+    nets = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)),
+                   *map(int, rng.choice(b.num_networks, 4, replace=False))})
+    qi_all, qe_all = oracle.queries(b.vac_ax)
+    for group in (1303, 0):
+        g = GpuBatch(b, max_synapses=int(b.vac_ax.sum()) + 1024)
+        stats = g.update(step=1, group=group, diag=True)
+        assert stats["searches"] == len(qi_all)
+        gt, gacc = R.relearn_get_requests(g.ctx)
+        dg = R.relearn_get_search_diag(g.ctx)
+        g.close()
+        for k in nets:
+            lo, hi = int(b.offsets[k]), int(b.offsets[k + 1])
+            t = oracle.Tree(b.x[lo:hi], b.y[lo:hi], b.z[lo:hi], id_base=lo)
+            t.reduce(b.vac_de[lo:hi])
+            mine = np.flatnonzero((qi_all >= lo) & (qi_all < hi))
+            sel = np.sort(rng.choice(mine, min(len(mine), 1500), replace=False))
+            ot, od = t.search_batch(float(b.sigma[k]), b.theta, b.seed, 1, qi_all[sel] - lo,
+                                    qe_all[sel], threads=8)
+            ot = np.where(ot >= 0, ot + lo, -1)
+            bad, exempt, exempt_diff = compare_targets(gt[sel], ot, od)
+            assert bad == 0, (k, group, bad, exempt, exempt_diff)
+            # ln S where no criterion test is within FP32 rounding of its tie (there the
+            # two frontiers can legitimately differ by a node)
+            fin = np.isfinite(od["ln_s0"]) & (od["margin_ac"] >= AC_MARGIN)
+            assert np.abs(dg["ln_s0"][sel][fin] - od["ln_s0"][fin]).max() < LNS_TOL, k
+            assert np.mean(od["margin_ac"] < AC_MARGIN) < 0.05
+            # acceptance of this network's requests (targets stay inside it): exact
+            # (priorities are keyed by the global source id; targets are local here)
+            oacc = oracle.accept(hi - lo, qi_all[mine], qe_all[mine],
+                                 np.where(gt[mine] >= 0, gt[mine] - lo, -1), b.vac_de[lo:hi],
+                                 b.seed, 1)
+            assert np.array_equal(gacc[mine], oacc), (k, group)
+            t.close()
