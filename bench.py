@@ -11,7 +11,10 @@ connectivity updates (bottom-up update, Barnes-Hut search, acceptance, apply),
 each followed by spike delivery (5 % of neurons spiking), then a deletion pass
 in which every element is retracted, which returns the network to empty so
 that every step does the same work. value = searches of all 10 updates / step
-time (device time, CUDA events); L2 is flushed between steps.
+time (device time, CUDA events); L2 is flushed between steps. The step's calls
+are captured once in a CUDA graph and replayed (--no-graph: direct calls); the
+search-kernel times for the roofline come from direct steps with the library's
+events.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload.
@@ -65,6 +68,8 @@ def parse():
     ap.add_argument("--group", type=int, default=0,
                     help="source neurons per octree walk in the search kernel (0 = default)")
     ap.add_argument("--workload", choices=["clusters", "batch", "diff"], default="clusters")
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="run the step as direct calls instead of one captured CUDA graph")
     ap.add_argument("--regroup", action="store_true",
                     help="two-phase search: restarts regrouped by subtree (RELEARN_FLAG_REGROUP)")
     ap.add_argument("--networks", type=int, default=256)
@@ -226,7 +231,7 @@ class Runner:
     def d2h_bytes(self):
         return 4 * self.net.n + 16
 
-    def step(self, e2e=False):
+    def step(self, e2e=False, timing=True):
         R, torch = self.R, self.torch
         if e2e:  # this step's inputs arrive from pinned host memory
             for name, dst in (("x", self.x), ("y", self.y), ("z", self.z),
@@ -242,7 +247,7 @@ class Runner:
         base = 1000 * self.step_index
         for u in range(UPDATES_PER_STEP):
             p = R.params(self.net.sigma, self.theta, self.net.seed, base + u,
-                         R.FLAG_TIMING | self.extra_flags, self.group)
+                         (R.FLAG_TIMING if timing else 0) | self.extra_flags, self.group)
             R.relearn_update_connectivity(self.ctx, p, self.vac_ax, self.vac_de, self.type)
             R.relearn_deliver_spikes(self.ctx, self.spiked[u], self.input)
         p = R.params(self.net.sigma, self.theta, self.net.seed, base + 999)
@@ -255,6 +260,48 @@ class Runner:
     def counters(self):
         s = self.R.relearn_get_last_stats(self.ctx)
         return s["searches_total"], s["evals_total"], s["walk_steps_total"]
+
+    def capture(self):
+        """The whole step (vacancy reset, build, 10 updates with delivery, deletion) as
+        one CUDA graph; every replay recomputes everything (same inputs, same draws)."""
+        torch = self.torch
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step(timing=False)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step(timing=False)
+        torch.cuda.synchronize()
+
+    def timed_graph(self, steps, e2e):
+        torch = self.torch
+        st = torch.cuda.current_stream()
+        total_ms = 0.0
+        q0, e0, w0 = self.counters()
+        for _ in range(steps):
+            self.flush.zero_()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            if e2e:  # this step's inputs arrive from pinned host memory
+                for name, dst in (("x", self.x), ("y", self.y), ("z", self.z),
+                                  ("vac_ax", self.vac_ax0), ("vac_de", self.vac_de0),
+                                  ("type", self.type), ("retract", self.retract)):
+                    dst.copy_(self.h[name], non_blocking=True)
+                for u in range(UPDATES_PER_STEP):
+                    self.spiked[u].copy_(self.h["spiked"][u], non_blocking=True)
+            self.graph.replay()
+            if e2e:
+                self.h_out.copy_(self.input, non_blocking=True)
+            b.record(st)
+            torch.cuda.synchronize()
+            total_ms += a.elapsed_time(b)
+        q1, e1, w1 = self.counters()
+        return {"ms": total_ms, "searches": q1 - q0, "evals": e1 - e0, "walk_steps": w1 - w0}
 
     def timed(self, steps, e2e):
         torch = self.torch
@@ -389,20 +436,33 @@ def run_ours(args):
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
+    if args.graph:
+        # search-kernel times (library events) come from direct steps; the step time
+        # from graph replays of the same step
+        res_k = run.timed(args.steps, e2e=False)
+        run.capture()
+        for _ in range(max(args.warmup, 3)):
+            run.graph.replay()
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
     clocks = ClockSampler(device.index)
     clocks.start()
-    res = run.timed(args.steps, e2e=False)
+    res = run.timed_graph(args.steps, e2e=False) if args.graph else run.timed(args.steps, False)
     clk = clocks.stop()
+    if args.graph:
+        res.update({k: res_k[k] for k in ("kernel_ms", "kernel_launches", "launches")})
     if ws > 1:
         dist.barrier()
     units, secs = aggregate(res["searches"], res["ms"] / 1000.0, ws, device)
     e2e = None
     if not args.no_e2e:
-        run.step(e2e=True)
+        if not args.graph:
+            run.step(e2e=True)
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
-        r2 = run.timed(args.steps, e2e=True)
+        r2 = run.timed_graph(args.steps, e2e=True) if args.graph else run.timed(args.steps, True)
         u2, s2 = aggregate(r2["searches"], r2["ms"] / 1000.0, ws, device)
         e2e = {"value": u2 / s2, "unit": UNIT, "h2d_bytes_per_step": run.h2d_bytes(),
                "d2h_bytes_per_step": run.d2h_bytes()}
@@ -443,6 +503,8 @@ def run_ours(args):
                 "evals_per_search": res["evals"] / max(res["searches"], 1),
                 "search_group": args.group or "default",
                 "restarts": "regrouped by subtree" if args.regroup else "inline",
+                "execution": "one CUDA graph replay per step" if args.graph else
+                             "direct calls (one C-ABI call per operation)",
                 "walk_steps_per_search": res["walk_steps"] / max(res["searches"], 1)}),
             "clocks": clk, "e2e": e2e, "gpu_launches": res["launches"],
             "roofline": roof, "cpu_baseline": cpu}
