@@ -119,6 +119,20 @@ def workload_config(net, theta, extra=None):
     return cfg
 
 
+def warm(fn, steps, min_seconds=2.0):
+    """At least `steps` untimed calls, and at least `min_seconds` of them: the first
+    process on a fresh GPU runs a few percent slow for its first second or so."""
+    import torch
+    t0 = time.perf_counter()
+    k = 0
+    while k < steps or time.perf_counter() - t0 < min_seconds:
+        fn()
+        k += 1
+        if k >= steps:
+            torch.cuda.synchronize()
+    return k
+
+
 # ---------------------------------------------------------------- distributed
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -431,8 +445,7 @@ def run_ours(args):
     from paper_2509_26193_gb300 import relearn as R
     run = Runner(net, args.theta, device, args.group, R.FLAG_REGROUP if args.regroup else 0)
     prof = first_update_profile(run)
-    for _ in range(max(args.warmup, 3)):
-        run.step()
+    warm(run.step, max(args.warmup, 3))
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -441,8 +454,7 @@ def run_ours(args):
         # from graph replays of the same step
         res_k = run.timed(args.steps, e2e=False)
         run.capture()
-        for _ in range(max(args.warmup, 3)):
-            run.graph.replay()
+        warm(run.graph.replay, max(args.warmup, 3))
         torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -691,8 +703,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     q1, e1 = run.counters()
     run.capture()
-    for _ in range(max(args.warmup, 3)):
-        run.graph.replay()
+    warm(run.graph.replay, max(args.warmup, 3))
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -817,8 +828,8 @@ def run_diff(args):
             tot += a.elapsed_time(b)
         return tot
 
-    for _ in range(max(args.warmup, 3)):
-        m = step()
+    warm(step, max(args.warmup, 3))
+    m = step()
     torch.cuda.synchronize()
     mean0 = float(m)
     e0 = R.relearn_get_last_stats(ctx)["length_evals_total"]
