@@ -156,7 +156,7 @@ __device__ int32_t lane_walk(const LenArgs &a, const Src &s, int32_t end, uint32
 }
 
 template <bool kBack>
-__global__ void __launch_bounds__(256) length_kernel(LenArgs a)
+__global__ void __launch_bounds__(256, 6) length_kernel(LenArgs a)
 {
     const int32_t A = (int32_t)*a.d_total;
     const int lane = threadIdx.x & 31;
