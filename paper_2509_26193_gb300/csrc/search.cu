@@ -45,11 +45,17 @@ constexpr float kTiny = 8.673617e-19f; // 2^-60
 // when they lie in one cell of depth >= kSpreadDepth, else groups of 8 do when each of
 // those fits such a cell, else every lane walks alone.
 constexpr int kSpreadDepth = 4;
-constexpr int kSpreadDepth8 = 4;
-// The split kernel (one warp per source) serves updates with at most kSplitWaves
-// sources per resident warp of the union kernel (a sweep on the 2^20-neuron
-// clustered network: 1 to 2 best; at 8 and more the split kernel is slower).
-constexpr int kSplitWaves = 2;
+constexpr int kSpreadDepth8 = 3;
+// The default also looks at how many sources the update has, per resident warp of
+// the union kernel (W). Per-update sweeps on the 2^20-neuron clustered network
+// (ten successive updates, 907k down to 2.4k sources): with fewer than kSplitWaves
+// * W sources the split kernel (one warp per source) wins; below kLaneWaves * W
+// every lane walking alone (32 loads in flight per warp) beats the unions, which
+// are latency-bound when few warps are resident; below kNo8Waves * W unions of 8
+// lose to lanes walking alone.
+constexpr int kSplitWaves = 1;
+constexpr int kLaneWaves = 8;
+constexpr int kNo8Waves = 40;
 
 // A node of depth d is accepted iff d^2 > thr0 / 4^d, thr0 = (root length / theta)^2
 // rounded to FP32 (see NodeTopo::shift). theta = 0 accepts no inner node.
@@ -163,6 +169,8 @@ struct SearchArgs {
     int spread_depth;  // a union of 32 needs all sources in one cell this deep
     int spread_depth8; // else a union of 8 needs its sources in one cell this deep
     int32_t split_below; // with forced_group 0: split kernel for at most this many sources
+    int32_t lane_below;  // default only: every lane walks alone below this many sources
+    int32_t no8_below;   // default only: no unions of 8 below this many sources
     // deferred restarts (RELEARN_FLAG_REGROUP): searches whose first draw is an inner
     // node are queued here and finished after a sort by that node (subtree order)
     int defer;
@@ -382,7 +390,9 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
         // ---- walk width: Morton codes are sorted, so the first and last code of a
         // range bound the cell that holds all of it; a union never spans two networks
         int G = a.forced_group;
-        if (G == 0) {
+        if (G == 0 && A < a.lane_below) {
+            G = 1;
+        } else if (G == 0) {
             uint32_t code = live ? a.codes[s] : 0u;
             code = __shfl_sync(0xffffffffu, code, live ? lane : last);
             const uint32_t c0 = __shfl_sync(0xffffffffu, code, 0);
@@ -393,7 +403,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                 const uint32_t f = __shfl_sync(0xffffffffu, code, lane & ~7);
                 const uint32_t l = __shfl_sync(0xffffffffu, code, lane | 7);
                 const int cp8 = __reduce_min_sync(0xffffffffu, morton_common_digits(f, l));
-                G = !mixed8 && cp8 >= a.spread_depth8 ? 8 : 1;
+                G = !mixed8 && cp8 >= a.spread_depth8 && A >= a.no8_below ? 8 : 1;
             }
         } else if (kBatched && G > 1 && n0 != n31) {
             // a fixed width whose groups would span networks: the widest that does not
@@ -953,11 +963,13 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
         return e;
     if (per_sm < 1) per_sm = 1;
     if (per_sm_split < 1) per_sm_split = 1;
-    // the union kernel serves 32 sources per warp; below kSplitWaves sources per
-    // resident warp it would leave the GPU mostly idle
+    // the union kernel serves 32 sources per warp; with few sources per resident warp
+    // it would leave the GPU mostly idle (kernel choice and widths: see kSplitWaves)
     const int64_t warps = (int64_t)c->num_sms * per_sm * 8;
-    a.split_below = sg >= 3000 ? (int32_t)std::min<int64_t>((int64_t)(sg - 3000) * 1024, 1 << 30)
-                               : (int32_t)std::min<int64_t>(warps * kSplitWaves, 1 << 30);
+    auto cap = [](int64_t v) { return (int32_t)std::min<int64_t>(v, 1 << 30); };
+    a.split_below = sg >= 3000 ? cap((int64_t)(sg - 3000) * 1024) : cap(warps * kSplitWaves);
+    a.lane_below = sg == 0 ? cap(warps * kLaneWaves) : 0;
+    a.no8_below = sg == 0 ? cap(warps * kNo8Waves) : 0;
     // exactly one of the two kernels does the work (each reads the source count)
     kern<<<c->num_sms * per_sm, 256, 0, st>>>(a);
     note_launch();
