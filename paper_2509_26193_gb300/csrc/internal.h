@@ -140,6 +140,16 @@ enum { I32_N = 0, I32_Q, I32_NSYN, I32_NEW, I32_NODES, I32_WORK, I32_ACTIVE, I32
 
 namespace rl {
 
+// Blocks for a grid-stride loop over n items: enough to cover n, at most 32 per SM.
+inline unsigned grid_for(int64_t n, int threads, int num_sms)
+{
+    int64_t b = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms * 32;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
 // api.cu --------------------------------------------------------------------
 // Counts kernel launches made by the library (reported by relearn_launch_count).
 void note_launch();

@@ -32,15 +32,6 @@ namespace {
 constexpr float kTinyL = 8.673617e-19f; // 2^-60: below this S is redone with a shift
 constexpr int kUnionDepth = 4;          // 32 sources in one cell this deep share a walk
 
-inline unsigned grid_for(int64_t n, int threads, int num_sms)
-{
-    int64_t b = (n + threads - 1) / threads;
-    int64_t cap = (int64_t)num_sms * 32;
-    if (b > cap) b = cap;
-    if (b < 1) b = 1;
-    return (unsigned)b;
-}
-
 struct LenArgs {
     const Node *__restrict__ nodes;
     const float4 *__restrict__ pos;

@@ -220,8 +220,6 @@ __global__ void split_keys_kernel(const uint64_t *__restrict__ keys, int64_t n,
     }
 }
 
-
-
 __global__ void gather_pos_kernel(const float *__restrict__ x, const float *__restrict__ y,
                                   const float *__restrict__ z, const int32_t *__restrict__ perm,
                                   int64_t n, float4 *__restrict__ pos)
@@ -536,15 +534,6 @@ __global__ void reduce_nodes_kernel(Node *__restrict__ nodes, const int32_t *__r
         }
         nodes[v].t.icount = (int32_t)s.c;
     }
-}
-
-inline unsigned grid_for(int64_t n, int threads, int num_sms)
-{
-    int64_t b = (n + threads - 1) / threads;
-    int64_t cap = (int64_t)num_sms * 32;
-    if (b > cap) b = cap;
-    if (b < 1) b = 1;
-    return (unsigned)b;
 }
 
 } // namespace

@@ -862,15 +862,6 @@ __global__ void __launch_bounds__(256) bh_restart_kernel(SearchArgs a, const uin
                   (unsigned long long)my_evals);
 }
 
-inline unsigned grid_for(int64_t n, int threads, int num_sms)
-{
-    int64_t b = (n + threads - 1) / threads;
-    int64_t cap = (int64_t)num_sms * 32;
-    if (b > cap) b = cap;
-    if (b < 1) b = 1;
-    return (unsigned)b;
-}
-
 } // namespace
 
 cudaError_t search_constants(relearn_ctx *c, const relearn_params &p, cudaStream_t st)

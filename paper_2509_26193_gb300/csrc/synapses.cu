@@ -19,15 +19,6 @@ namespace rl {
 
 namespace {
 
-inline unsigned grid_for(int64_t n, int threads, int num_sms)
-{
-    int64_t b = (n + threads - 1) / threads;
-    int64_t cap = (int64_t)num_sms * 32;
-    if (b > cap) b = cap;
-    if (b < 1) b = 1;
-    return (unsigned)b;
-}
-
 #define GRID_STRIDE(i, n)                                                                         \
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n);                     \
          i += (int64_t)gridDim.x * blockDim.x)
