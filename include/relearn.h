@@ -58,8 +58,9 @@ typedef struct relearn_ctx relearn_ctx;
  *             the octree together in the search kernel: 1, 8, 16 or 32 for a fixed width;
  *             2 = one source per warp, its root frontier split over the 32 lanes;
  *             0 = the default: one source per warp when the update has few sources
- *             (at most one per resident warp), every lane alone up to 8 per resident warp,
- *             else chosen per warp from how close its sources are;
+ *             (at most one per resident warp) and the tree is large (2^17 nodes or more),
+ *             every lane alone up to 8 sources per resident warp, else chosen per warp
+ *             from how close its sources are;
  *             1000 + 100 * d32 + d8 (d32, d8 = 0..10) = chosen per warp: 32 together when
  *             they share a cell of depth >= d32, else 8 together when they share a cell of
  *             depth >= d8, else one by one;

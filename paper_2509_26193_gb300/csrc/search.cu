@@ -54,6 +54,9 @@ constexpr int kSpreadDepth8 = 3;
 // are latency-bound when few warps are resident; below kNo8Waves * W unions of 8
 // lose to lanes walking alone.
 constexpr int kSplitWaves = 1;
+// Small trees have small frontiers, where the split kernel's expansion and prefix
+// cost more than they save (4096-neuron cube: 0.81 ms split, 0.52 ms union).
+constexpr int64_t kSplitMinNodes = int64_t(1) << 17;
 constexpr int kLaneWaves = 8;
 constexpr int kNo8Waves = 40;
 
@@ -169,6 +172,8 @@ struct SearchArgs {
     int spread_depth;  // a union of 32 needs all sources in one cell this deep
     int spread_depth8; // else a union of 8 needs its sources in one cell this deep
     int32_t split_below; // with forced_group 0: split kernel for at most this many sources
+    int64_t split_min_nodes; // ... and at least this many tree nodes (small trees: unions)
+    const int64_t *num_nodes;
     int32_t lane_below;  // default only: every lane walks alone below this many sources
     int32_t no8_below;   // default only: no unions of 8 below this many sources
     // deferred restarts (RELEARN_FLAG_REGROUP): searches whose first draw is an inner
@@ -181,6 +186,13 @@ struct SearchArgs {
     int32_t *rq_src;  // [slot] Morton position of the source
     int32_t *rq_count;
 };
+
+// Which of the two search kernels serves this launch (both read the same counts).
+__device__ __forceinline__ bool split_launch(const SearchArgs &a, int32_t A)
+{
+    return a.forced_group == 2 ||
+           (a.forced_group == 0 && A <= a.split_below && *a.num_nodes >= a.split_min_nodes);
+}
 
 struct WalkOut {
     float sum;
@@ -342,8 +354,7 @@ template <bool kBatched>
 __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kernel(SearchArgs a)
 {
     const int32_t A = *a.d_A;
-    if (a.forced_group == 2 || (a.forced_group == 0 && A <= a.split_below))
-        return; // bh_split_kernel serves this launch
+    if (split_launch(a, A)) return; // bh_split_kernel serves this launch
     const int lane = threadIdx.x & 31;
     int32_t root = 0, root_end = 0;
     uint32_t thr0 = 0;
@@ -629,7 +640,7 @@ __global__ void __launch_bounds__(256) bh_split_kernel(SearchArgs a)
     __shared__ SplitItem s_items[8][2][kSplitCap];
     __shared__ double s_pref[8][kSplitCap];
     const int32_t A = *a.d_A;
-    if (!(a.forced_group == 2 || (a.forced_group == 0 && A <= a.split_below))) return;
+    if (!split_launch(a, A)) return; // bh_search_kernel serves this launch
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int64_t my_evals = 0, my_steps = 0;
     int32_t root = 0;
@@ -959,6 +970,8 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     const int64_t warps = (int64_t)c->num_sms * per_sm * 8;
     auto cap = [](int64_t v) { return (int32_t)std::min<int64_t>(v, 1 << 30); };
     a.split_below = sg >= 3000 ? cap((int64_t)(sg - 3000) * 1024) : cap(warps * kSplitWaves);
+    a.split_min_nodes = sg == 0 ? kSplitMinNodes : 0;
+    a.num_nodes = c->d_i64 + I64_NODES;
     a.lane_below = sg == 0 ? cap(warps * kLaneWaves) : 0;
     a.no8_below = sg == 0 ? cap(warps * kNo8Waves) : 0;
     // exactly one of the two kernels does the work (each reads the source count)
