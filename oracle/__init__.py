@@ -377,3 +377,23 @@ def mean_length(tree: Tree, sigma, theta, vac_ax, vac_de, grad=True, threads=1):
     if grad:
         out["g"] = np.stack(g, 1)
     return out
+
+
+def update_connectivity_typed(tree: Tree, vac_ax, vac_de_exc, vac_de_inh, type_, sigma, theta,
+                              seed, step, syn: Synapses, threads=1):
+    """Typed dendrite pools (reading R16): each neuron has vacant excitatory and
+    inhibitory dendritic elements; the tree holds two pools (counts and centroids
+    per pool), an excitatory axon (type 0) searches the excitatory pool and an
+    inhibitory axon the inhibitory one, and each pool of a target accepts only the
+    requests made to it. The two pools never interact, so the update is the plain
+    update of Sec. III-A/III-B once per pool, restricted to that pool's axons, with
+    the same Philox counters. Updates vac_ax and both pools in place; returns
+    {"exc": ..., "inh": ...}, each the dict of update_connectivity for that pool."""
+    type_ = np.asarray(type_, np.uint8)
+    out = {}
+    for kind, name, vde in ((0, "exc", vac_de_exc), (1, "inh", vac_de_inh)):
+        va = np.where(type_ == kind, vac_ax, 0).astype(np.int32)
+        out[name] = update_connectivity(tree, va, vde, type_, sigma, theta, seed, step, syn,
+                                        threads=threads)
+        vac_ax[type_ == kind] = va[type_ == kind]
+    return out

@@ -51,6 +51,9 @@
  *       is the attraction-weighted mean distance to the centroids of its root frontier
  *       (the first draw's candidates); its gradient treats the criterion and the tree
  *       topology as constant (see orc_mean_length)
+ *   R16 typed dendrite pools (a variant; the paper's request carries a cell type,
+ *       Sec. III-B): excitatory axons search excitatory dendritic elements, inhibitory
+ *       axons inhibitory ones; composed from the functions here in oracle/__init__.py
  *
  * Every function here has a pin in the CPU test suite (tests/test_oracle_*.py).
  */
