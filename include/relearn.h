@@ -204,6 +204,21 @@ relearn_status relearn_update_connectivity(relearn_ctx *ctx, const relearn_param
                                            const uint8_t *type, relearn_update_stats *stats,
                                            void *stream);
 
+/* Typed dendrite pools (a variant of the update above): every neuron has vacant excitatory
+ * (vac_de_exc) and inhibitory (vac_de_inh) dendritic elements; an excitatory axon (type 0)
+ * searches a tree of the excitatory pool only, an inhibitory axon (type 1) the inhibitory
+ * pool, and each pool of a target accepts only the requests made to it (the request's cell
+ * type, Sec. III-B, selects the pool). The pools never interact, so this is the update
+ * above once per pool on the same topology, restricted to that pool's axons, with the same
+ * Philox counters; vac_ax and both pools are updated in place, synapse sign = source type.
+ * relearn_get_requests / relearn_get_search_diag then describe the inhibitory pass.
+ * stats (host or NULL) sums the two passes. Errors: as relearn_update_connectivity; the two
+ * pool arrays must be different. */
+relearn_status relearn_update_connectivity_typed(relearn_ctx *ctx, const relearn_params *params,
+                                                 int32_t *vac_ax, int32_t *vac_de_exc,
+                                                 int32_t *vac_de_inh, const uint8_t *type,
+                                                 relearn_update_stats *stats, void *stream);
+
 /* Deletion pass (Sec. III-A "Update of synapses", first sub-phase).
  *   retract_ax, retract_de  device int32[n] (>= 0): elements each neuron retracts.
  *   vac_ax, vac_de          device int32[n], in/out.

@@ -424,6 +424,52 @@ relearn_status relearn_update_connectivity(relearn_ctx *c, const relearn_params 
     return RELEARN_OK;
 }
 
+relearn_status relearn_update_connectivity_typed(relearn_ctx *c, const relearn_params *p,
+                                                 int32_t *vac_ax, int32_t *vac_de_exc,
+                                                 int32_t *vac_de_inh, const uint8_t *type,
+                                                 relearn_update_stats *stats, void *stream)
+{
+    if (!c) return RELEARN_ERR_INVALID_ARG;
+    if (!c->built) return fail(c, RELEARN_ERR_STATE, "update before build_octree");
+    if (!params_ok(p)) return fail(c, RELEARN_ERR_INVALID_ARG, "update_typed: bad params");
+    if (!vac_ax || !vac_de_exc || !vac_de_inh || !type)
+        return fail(c, RELEARN_ERR_INVALID_ARG, "update_typed: NULL array");
+    if (vac_de_exc == vac_de_inh)
+        return fail(c, RELEARN_ERR_INVALID_ARG, "update_typed: the two pools must differ");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(c, RELEARN_ERR_CUDA, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *part = c->d_need_ax; // scratch [n]: free outside deletion
+    relearn_update_stats sum{};
+    for (int kind = 0; kind < 2; ++kind) {
+        CK(select_type(c, vac_ax, type, kind, part, st), "select type");
+        relearn_update_stats one{};
+        relearn_status s = relearn_update_connectivity(c, p, part, kind ? vac_de_inh : vac_de_exc,
+                                                       type, stats ? &one : nullptr, stream);
+        if (s != RELEARN_OK) return s;
+        CK(merge_type(c, part, type, kind, vac_ax, st), "merge type");
+        if (stats) {
+            sum.searches += one.searches;
+            sum.failed += one.failed;
+            sum.requests_declined += one.requests_declined;
+            sum.formed += one.formed;
+            sum.synapses = one.synapses;
+            sum.ms_reduce += one.ms_reduce;
+            sum.ms_search += one.ms_search;
+            sum.ms_search_kernel += one.ms_search_kernel;
+            sum.ms_accept += one.ms_accept;
+            sum.ms_apply += one.ms_apply;
+            sum.ms_total += one.ms_total;
+            sum.searches_total = one.searches_total;
+            sum.evals_total = one.evals_total;
+            sum.walk_steps_total = one.walk_steps_total;
+            sum.length_evals_total = one.length_evals_total;
+        }
+    }
+    if (stats) *stats = sum;
+    return RELEARN_OK;
+}
+
 relearn_status relearn_mean_length(relearn_ctx *c, const relearn_params *p,
                                    const int32_t *vac_ax, const int32_t *vac_de, float *ell,
                                    double *mean, void *stream)

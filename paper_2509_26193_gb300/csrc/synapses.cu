@@ -512,6 +512,46 @@ cudaError_t delete_synapses(relearn_ctx *c, const relearn_params &p, const int32
     return rebuild_views(c, st);
 }
 
+namespace {
+
+// Typed dendrite pools: the axons of one type, and writing them back.
+__global__ void select_type_kernel(const int32_t *__restrict__ vac_ax,
+                                   const uint8_t *__restrict__ type, int kind, int64_t n,
+                                   int32_t *__restrict__ out)
+{
+    GRID_STRIDE(i, n) out[i] = type[i] == kind ? vac_ax[i] : 0;
+}
+
+__global__ void merge_type_kernel(const int32_t *__restrict__ part,
+                                  const uint8_t *__restrict__ type, int kind, int64_t n,
+                                  int32_t *__restrict__ vac_ax)
+{
+    GRID_STRIDE(i, n)
+    {
+        if (type[i] == kind) vac_ax[i] = part[i];
+    }
+}
+
+} // namespace
+
+cudaError_t select_type(relearn_ctx *c, const int32_t *vac_ax, const uint8_t *type, int kind,
+                        int32_t *out, cudaStream_t st)
+{
+    select_type_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(vac_ax, type, kind, c->n,
+                                                                        out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t merge_type(relearn_ctx *c, const int32_t *part, const uint8_t *type, int kind,
+                       int32_t *vac_ax, cudaStream_t st)
+{
+    merge_type_kernel<<<grid_for(c->n, 256, c->num_sms), 256, 0, st>>>(part, type, kind, c->n,
+                                                                       vac_ax);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t deliver_spikes(relearn_ctx *c, const uint8_t *spiked, int32_t *input,
                            cudaStream_t st)
 {

@@ -72,6 +72,8 @@ _SIGS = {
                                 ctypes.POINTER(_I64), _P],
     "relearn_deliver_spikes": [_P, _P, _P, _P],
     "relearn_mean_length": [_P, ctypes.POINTER(relearn_params), _P, _P, _P, _P, _P],
+    "relearn_update_connectivity_typed": [_P, ctypes.POINTER(relearn_params), _P, _P, _P, _P,
+                                          ctypes.POINTER(relearn_update_stats), _P],
     "relearn_mean_length_backward": [_P, _P, _P, _P, _P, _P, _P, _P, _P],
     "relearn_deliver_rates": [_P, _P, ctypes.c_uint64, ctypes.c_uint64, _P, _P],
     "relearn_get_synapses": [_P, _I64, ctypes.POINTER(_I64), _P, _P, _P],
@@ -234,6 +236,22 @@ def relearn_build_octree(ctx, x, y, z, vac_de=None, box_lo=None, box_hi=None, st
     _raise(ctx, st, "relearn_build_octree")
     ctx.n = n
     ctx.num_networks = 1
+
+
+def relearn_update_connectivity_typed(ctx, prm, vac_ax, vac_de_exc, vac_de_inh, type_,
+                                      stats=False, stream=None):
+    torch = _torch()
+    n = ctx.n
+    a = _dev_ptr(vac_ax, torch.int32, n, "vac_ax")
+    de = _dev_ptr(vac_de_exc, torch.int32, n, "vac_de_exc")
+    di = _dev_ptr(vac_de_inh, torch.int32, n, "vac_de_inh")
+    t = _dev_ptr(type_, torch.uint8, n, "type")
+    s = relearn_update_stats() if stats else None
+    st = lib().relearn_update_connectivity_typed(ctx.handle, ctypes.byref(prm), a, de, di, t,
+                                                 ctypes.byref(s) if s is not None else None,
+                                                 _stream(stream))
+    _raise(ctx, st, "relearn_update_connectivity_typed")
+    return s.as_dict() if s is not None else None
 
 
 def relearn_build_octree_batch(ctx, offsets, x, y, z, vac_de=None, stream=None):
