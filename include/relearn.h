@@ -61,13 +61,15 @@ typedef struct relearn_ctx relearn_ctx;
  *   seed      key of every Philox4x32-10 draw.
  *   step      update index (< 2^32), part of every Philox counter.
  *   flags     RELEARN_FLAG_* bits.
- *   search_group  tuning only (results do not depend on it): how many source neurons walk
- *             the octree together in the search kernel: 1, 8, 16 or 32 for a fixed width;
- *             2 = one source per warp, its root frontier split over the 32 lanes;
- *             0 = the default: one source per warp when the update has few sources
- *             (at most one per resident warp) and the tree is large (2^17 nodes or more),
- *             every lane alone up to 8 sources per resident warp, else chosen per warp
- *             from how close its sources are;
+ *   search_group  tuning only: how many source neurons walk the octree together in the
+ *             search kernel. The requests do not depend on it, except that one source per
+ *             warp (2) sums its candidates in another association, so its draws may
+ *             differ from the others' within rounding of a cumulative boundary.
+ *             1, 8, 16 or 32 = a fixed width;
+ *             2 = one source per warp, its frontier walk shared out over the 32 lanes;
+ *             0 = the default: one source per warp when the update has at most 9 sources
+ *             per resident warp of the union kernel, else chosen per warp from how close
+ *             its sources are;
  *             1000 + 100 * d32 + d8 (d32, d8 = 0..10) = chosen per warp: 32 together when
  *             they share a cell of depth >= d32, else 8 together when they share a cell of
  *             depth >= d8, else one by one;

@@ -47,17 +47,13 @@ constexpr float kTiny = 8.673617e-19f; // 2^-60
 constexpr int kSpreadDepth = 4;
 constexpr int kSpreadDepth8 = 3;
 // The default also looks at how many sources the update has, per resident warp of
-// the union kernel (W). Per-update sweeps on the 2^20-neuron clustered network
-// (ten successive updates, 907k down to 2.4k sources): with fewer than kSplitWaves
-// * W sources the split kernel (one warp per source) wins; below kLaneWaves * W
-// every lane walking alone (32 loads in flight per warp) beats the unions, which
-// are latency-bound when few warps are resident; below kNo8Waves * W unions of 8
-// lose to lanes walking alone.
-constexpr int kSplitWaves = 1;
-// Small trees have small frontiers, where the split kernel's expansion and prefix
-// cost more than they save (4096-neuron cube: 0.81 ms split, 0.52 ms union).
-constexpr int64_t kSplitMinNodes = int64_t(1) << 17;
-constexpr int kLaneWaves = 8;
+// the union kernel (W = 7,296 on 152 SMs). Per-update sweeps on the 2^20-neuron
+// clustered network (ten successive updates, 907k down to 2.4k sources): with at
+// most kSplitWaves * W sources the split kernel (one warp per source) wins (61.8k
+// sources: 1.67 ms against 1.84 ms; 162k: 4.73 ms against 2.46 ms), on small trees
+// as well (4096-neuron cube, 4096 sources: 0.10 ms against 0.46 ms); below
+// kNo8Waves * W unions of 8 lose to lanes walking alone.
+constexpr int kSplitWaves = 9;
 constexpr int kNo8Waves = 40;
 
 // A node of depth d is accepted iff d^2 > thr0 / 4^d, thr0 = (root length / theta)^2
@@ -172,9 +168,6 @@ struct SearchArgs {
     int spread_depth;  // a union of 32 needs all sources in one cell this deep
     int spread_depth8; // else a union of 8 needs its sources in one cell this deep
     int32_t split_below; // with forced_group 0: split kernel for at most this many sources
-    int64_t split_min_nodes; // ... and at least this many tree nodes (small trees: unions)
-    const int64_t *num_nodes;
-    int32_t lane_below;  // default only: every lane walks alone below this many sources
     int32_t no8_below;   // default only: no unions of 8 below this many sources
     // deferred restarts (RELEARN_FLAG_REGROUP): searches whose first draw is an inner
     // node are queued here and finished after a sort by that node (subtree order)
@@ -191,7 +184,7 @@ struct SearchArgs {
 __device__ __forceinline__ bool split_launch(const SearchArgs &a, int32_t A)
 {
     return a.forced_group == 2 ||
-           (a.forced_group == 0 && A <= a.split_below && *a.num_nodes >= a.split_min_nodes);
+           (a.forced_group == 0 && A <= a.split_below);
 }
 
 struct WalkOut {
@@ -401,9 +394,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
         // ---- walk width: Morton codes are sorted, so the first and last code of a
         // range bound the cell that holds all of it; a union never spans two networks
         int G = a.forced_group;
-        if (G == 0 && A < a.lane_below) {
-            G = 1;
-        } else if (G == 0) {
+        if (G == 0) {
             uint32_t code = live ? a.codes[s] : 0u;
             code = __shfl_sync(0xffffffffu, code, live ? lane : last);
             const uint32_t c0 = __shfl_sync(0xffffffffu, code, 0);
@@ -564,84 +555,217 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
 // kernel would leave most of the GPU idle while each lane walks a whole frontier
 // alone, one dependent node load after another).
 //
-// The warp first expands the source's frontier top-down, breadth first, keeping
-// an ordered list (pre-order) of items: accepted candidates with their
-// attraction, and subtrees of rejected nodes still to be expanded. Each round
-// replaces every subtree item by its children's items (lanes in parallel, order
-// kept by a warp prefix sum) until there are at least kSplitTasks subtrees (or
-// none, or the list is full); nodes with more than 8 children (buckets) stay
-// subtrees. The lanes then walk the remaining subtrees (stackless, compensated
-// FP32 partial sums), the list's inclusive prefix is scanned in FP64 (S is its
-// total), and each lane draws one of the source's searches: the item holding
-// u * S by binary search, inside a subtree by repeating that subtree's partial
-// sum, then restarts as in the union kernel. The candidates and their order are
-// the union kernel's; only the association of the FP32/FP64 sums differs, so a
-// draw can differ from the union kernel's only within rounding of a cumulative
-// boundary.
-constexpr int kSplitCap = 128;   // items per warp
-constexpr int kSplitTasks = 48;  // stop expanding at this many subtrees
-constexpr int kSplitRounds = 12; // tree depth bound
-constexpr uint32_t kSub = 0x80000000u; // item is a subtree (node index in the low bits)
+// The source's frontier walk is shared out among the 32 lanes as contiguous
+// ranges of the pre-order node array. A walk over a range [b, e) is the plain
+// stackless walk started at b: b is always a node the source's walk visits (the
+// root's first child, or the escape of a node the walk descended into), so the
+// range holds exactly the source's candidates between b and e, in order. Lane 0
+// starts with [root + 1, root end); whenever a lane descends into a rejected node
+// p while other lanes are idle, it keeps [b, escape(p)) and hands the rest,
+// [escape(p), e), to an idle lane. Ranges therefore stay contiguous and are
+// linked in pre-order (each keeps the index of the range that follows it), and
+// work is rebalanced at every step instead of by a fixed partition.
+//
+// Each range's candidates are summed from zero in FP32 with Kahan compensation;
+// the ranges' partial sums then form an FP64 inclusive prefix in pre-order (S is
+// its total), and each lane draws one of the source's searches: the range holding
+// u * S by binary search, inside it by repeating its walk and partial sum, then
+// restarts as in the union kernel. The candidates and their order are the union
+// kernel's; only the association of the FP32/FP64 sums differs, so a draw can
+// differ from the union kernel's only within rounding of a cumulative boundary.
+constexpr int kSplitRanges = 512; // ranges per source (the list stops growing there)
+constexpr int kSplitMinRest = 64; // a rest of fewer nodes is not handed out
 
-struct SplitItem {
-    uint32_t node; // node index, | kSub for a subtree
-    float val;     // attraction (candidate) or partial sum (subtree, after its walk)
-};
-
-__device__ __forceinline__ int warp_excl_scan(int v, int &total)
+// The source's candidates in [b, e), compensated sum from zero, until the running
+// total exceeds rel: that candidate, else the last with weight, else -1. The same
+// arithmetic as bh_split_kernel's range walks, step for step.
+__device__ __forceinline__ int32_t range_find(const Node *__restrict__ nodes, int32_t b,
+                                              int32_t e, float3 x, int32_t self_node,
+                                              uint32_t thr0, float k2, float k2sh, float rel)
 {
-    const int lane = threadIdx.x & 31;
-    int inc = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
-    }
-    total = __shfl_sync(0xffffffffu, inc, 31);
-    return inc - v;
-}
-
-// A subtree item's walk: the source's candidates below node v, compensated sum
-// from zero (FIND: the first whose partial exceeds rel, else the last with weight).
-template <bool FIND>
-__device__ __forceinline__ int32_t subtree_walk(const Node *__restrict__ nodes, int32_t v,
-                                                float3 x, int32_t self_node, uint32_t thr0,
-                                                float k2, float k2sh, float rel, float &part,
-                                                float &dmin2, int32_t &evals)
-{
-    const int32_t end = __ldg(&nodes[v].t.escape);
-    int32_t p = v + 1, pick = -1;
+    int32_t p = b, pick = -1;
     float cum = 0.0f, comp = 0.0f;
-    while (p < end) {
+    while (p < e) {
         const float4 g = __ldg(reinterpret_cast<const float4 *>(&nodes[p].g));
         const int2 t = __ldg(reinterpret_cast<const int2 *>(&nodes[p].t));
         const float d2 = dist2(x, g);
         const bool has = g.w > 0.0f;
         const bool acc = has && (__float_as_uint(d2) + (uint32_t)t.y > thr0);
-        if (!FIND) evals += has ? 1 : 0;
         if (acc && p != self_node) {
             const float at = attraction(g.w, d2, k2, k2sh);
             kahan_add(cum, comp, at);
-            if (FIND) {
-                if (at > 0.0f) pick = p;
-                if (__fsub_rn(cum, comp) > rel) return p;
-            } else {
-                dmin2 = fminf(dmin2, d2);
-            }
+            if (at > 0.0f) pick = p;
+            if (__fsub_rn(cum, comp) > rel) return p;
         }
         p = (has && !acc) ? p + 1 : max(t.x, p + 1);
     }
-    part = __fsub_rn(cum, comp);
     return pick;
+}
+
+__device__ __forceinline__ int warp_sum_i(int v)
+{
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Per warp: the ranges of the current source and their order. The FP64 prefix of
+// the partial sums in pre-order is kept as 32 block starts: lane k sums the ranges
+// ord[k * per .. (k + 1) * per) on top of start[k] (see split_walk).
+struct SplitLists {
+    int32_t b[kSplitRanges];    // first node of each range
+    float part[kSplitRanges];   // its compensated partial sum
+    int16_t next[kSplitRanges]; // the range that follows it in pre-order (-1: last)
+    int16_t ord[kSplitRanges];  // ranges in pre-order
+    double start[32];           // prefix before each lane's block of ranges
+    int32_t give_b[32], give_e[32], give_next[32]; // hand-over slots of one step
+};
+constexpr size_t kSplitSmem = 8 * sizeof(SplitLists); // per block of 8 warps
+
+// The inclusive prefix of the ranges in pre-order, as split_walk forms it: the
+// first position q whose prefix exceeds tgt (tgt < S), and the prefix before q.
+__device__ __forceinline__ int split_locate(const SplitLists &L, int n_rec, double tgt,
+                                            double &base)
+{
+    const int per = (n_rec + 31) >> 5;
+    const int nb = (n_rec + per - 1) / per; // non-empty blocks
+    int k = 0;
+    for (int j = 1; j < nb; ++j)
+        if (L.start[j] <= tgt) k = j;
+    const int q0 = k * per, q1 = min(q0 + per, n_rec);
+    double run = 0.0;
+    for (int q = q0; q < q1; ++q) {
+        const double before = L.start[k] + run;
+        run += (double)L.part[L.ord[q]];
+        if (L.start[k] + run > tgt || q == q1 - 1) {
+            base = before;
+            return q;
+        }
+    }
+    base = L.start[k];
+    return q0;
+}
+
+// The shared walk of one source's frontier (see above). Every lane of the warp
+// calls it. Returns the number of ranges and S (every lane); own (this lane's
+// evaluations), dmin2 (nearest candidate this lane met) and steps (walk steps,
+// lane 0) accumulate.
+__device__ __forceinline__ int split_walk(const SearchArgs &a, SplitLists &L, int32_t root,
+                                          int32_t root_end, float3 x, int32_t self_node,
+                                          uint32_t thr0, float k2, float k2sh, int32_t &own,
+                                          float &dmin2, int64_t &steps, double &S)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    int32_t p = 0, e = 0, rid = -1, rnext = -1;
+    float cum = 0.0f, comp = 0.0f;
+    bool busy = false;
+    if (lane == 0) {
+        L.b[0] = root + 1;
+        L.part[0] = 0.0f;
+        L.next[0] = -1;
+        rid = 0;
+        p = root + 1;
+        e = root_end;
+        busy = p < e;
+    }
+    int n_rec = 1;
+    __syncwarp();
+    for (;;) {
+        bool split = false;
+        int32_t rest = 0;
+        if (busy) {
+            const float4 g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[p].g));
+            const int2 t = __ldg(reinterpret_cast<const int2 *>(&a.nodes[p].t));
+            const float d2 = dist2(x, g);
+            const bool has = g.w > 0.0f;
+            const bool acc = has && (__float_as_uint(d2) + (uint32_t)t.y > thr0);
+            own += has ? 1 : 0;
+            if (acc && p != self_node) {
+                kahan_add(cum, comp, attraction(g.w, d2, k2, k2sh));
+                dmin2 = fminf(dmin2, d2);
+            }
+            if (has && !acc) { // descend; the part after p's subtree may go to another lane
+                rest = max(t.x, p + 1);
+                split = e - rest >= kSplitMinRest;
+                p = p + 1;
+            } else {
+                p = max(t.x, p + 1);
+            }
+            if (p >= e) { // range done
+                L.part[rid] = __fsub_rn(cum, comp);
+                L.next[rid] = (int16_t)rnext;
+                busy = false;
+                split = false;
+            }
+        }
+        const uint32_t idle = __ballot_sync(0xffffffffu, !busy);
+        if (idle == 0xffffffffu) break;
+        steps += lane == 0 ? 1 : 0;
+        const uint32_t spl = __ballot_sync(0xffffffffu, split);
+        const int give = min(min(__popc(idle), __popc(spl)), kSplitRanges - n_rec);
+        if (give > 0) { // warp-uniform: the r-th splitting lane gives to the r-th idle lane
+            const int rs = __popc(spl & lt), ri = __popc(idle & lt);
+            if (split && rs < give) {
+                L.give_b[rs] = rest;
+                L.give_e[rs] = e;
+                L.give_next[rs] = rnext;
+                e = rest;
+                rnext = n_rec + rs;
+            }
+            __syncwarp();
+            if (!busy && ri < give) {
+                rid = n_rec + ri;
+                p = L.give_b[ri];
+                e = L.give_e[ri];
+                rnext = L.give_next[ri];
+                L.b[rid] = p;
+                cum = 0.0f;
+                comp = 0.0f;
+                busy = true;
+            }
+            __syncwarp();
+            n_rec += give;
+        }
+    }
+    __syncwarp();
+    // pre-order of the ranges: follow the links from the first one
+    if (lane == 0) {
+        int r = 0;
+        for (int pos = 0; pos < n_rec; ++pos) { // the links reach every range once
+            L.ord[pos] = (int16_t)(r >= 0 ? r : 0);
+            if (r >= 0) r = L.next[r];
+        }
+    }
+    __syncwarp();
+    // FP64 inclusive prefix in pre-order: lane k sums its block of ranges from zero
+    // (blk); its block starts at the left-to-right sum of blocks 0 .. k-1, and the
+    // prefix at position q of the block is start + (the block's running sum), so the
+    // last entry of block k equals block k + 1's start (the prefix is monotone)
+    const int per = (n_rec + 31) >> 5;
+    const int q0 = min(lane * per, n_rec), q1 = min(q0 + per, n_rec);
+    double blk = 0.0;
+    for (int q = q0; q < q1; ++q) blk += (double)L.part[L.ord[q]];
+    double start = 0.0;
+    for (int j = 0; j < 31; ++j) {
+        const double t = __shfl_sync(0xffffffffu, blk, j);
+        if (j < lane) start += t;
+    }
+    L.start[lane] = start;
+    const int nb = (n_rec + per - 1) / per;
+    S = __shfl_sync(0xffffffffu, start + blk, nb - 1);
+    __syncwarp();
+    return n_rec;
 }
 
 template <bool kBatched>
 __global__ void __launch_bounds__(256) bh_split_kernel(SearchArgs a)
 {
-    __shared__ SplitItem s_items[8][2][kSplitCap];
-    __shared__ double s_pref[8][kSplitCap];
+    extern __shared__ __align__(16) unsigned char s_raw[]; // kSplitSmem bytes
+    SplitLists *s_lists = reinterpret_cast<SplitLists *>(s_raw);
     const int32_t A = *a.d_A;
     if (!split_launch(a, A)) return; // bh_search_kernel serves this launch
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    SplitLists &L = s_lists[w];
     int64_t my_evals = 0, my_steps = 0;
     int32_t root = 0;
     uint32_t thr0 = 0;
@@ -665,115 +789,24 @@ __global__ void __launch_bounds__(256) bh_split_kernel(SearchArgs a)
             thr0 = __ldg(&a.sc[net].thr0);
             k2 = __ldg(&a.sc[net].k2);
         }
-        // ---- breadth-first expansion into an ordered item list
-        int cur = 0, L = 1;
-        if (lane == 0) s_items[w][0][0] = SplitItem{kSub | (uint32_t)root, 0.0f};
-        __syncwarp();
-        int32_t own = 0;
-        for (int round = 0; round < kSplitRounds; ++round) {
-            int n_sub = 0;
-            for (int b = 0; b < L; b += 32)
-                n_sub += __popc(__ballot_sync(0xffffffffu,
-                                              b + lane < L && (s_items[w][cur][b + lane].node & kSub)));
-            if (n_sub == 0 || n_sub >= kSplitTasks) break;
-            int total = 0, ev_round = 0;
-            bool over = false;
-            for (int b = 0; b < L; b += 32) {
-                const int it = b + lane;
-                SplitItem out[8];
-                int n_out = 0;
-                if (it < L) {
-                    const SplitItem item = s_items[w][cur][it];
-                    if (!(item.node & kSub)) {
-                        out[n_out++] = item;
-                    } else {
-                        const int32_t v = (int32_t)(item.node & ~kSub);
-                        const int32_t end = __ldg(&a.nodes[v].t.escape);
-                        int32_t c = v + 1, ev = 0;
-                        bool wide = false;
-                        while (c < end) {
-                            const float4 g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[c].g));
-                            const int2 t = __ldg(reinterpret_cast<const int2 *>(&a.nodes[c].t));
-                            if (g.w > 0.0f) {
-                                if (n_out == 8) { wide = true; break; }
-                                ++ev;
-                                const float d2 = dist2(x, g);
-                                if (__float_as_uint(d2) + (uint32_t)t.y > thr0) {
-                                    if (c != self_node)
-                                        out[n_out++] = SplitItem{(uint32_t)c,
-                                                                 attraction(g.w, d2, k2, 0.0f)};
-                                } else {
-                                    out[n_out++] = SplitItem{kSub | (uint32_t)c, 0.0f};
-                                }
-                            }
-                            c = max(t.x, c + 1);
-                        }
-                        if (wide) { // a bucket: keep it whole, its walk comes later
-                            n_out = 1;
-                            out[0] = item;
-                        } else {
-                            ev_round += ev;
-                        }
-                    }
-                }
-                int chunk_total;
-                const int off = total + warp_excl_scan(n_out, chunk_total);
-                if (total + chunk_total > kSplitCap) over = true;
-                else
-                    for (int q = 0; q < n_out; ++q) s_items[w][cur ^ 1][off + q] = out[q];
-                total += chunk_total;
-            }
-            __syncwarp();
-            if (over) break; // the list would overflow: walk what we have
-            for (int o = 16; o; o >>= 1) ev_round += __shfl_xor_sync(0xffffffffu, ev_round, o);
-            own += ev_round;
-            cur ^= 1;
-            L = total;
-        }
-        // ---- walk the subtrees, then the inclusive prefix (FP64) over the list
+        const int32_t root_end = __ldg(&a.nodes[root].t.escape);
         float k2sh = 0.0f;
         double S = 0.0;
-        int32_t own_walk = 0;
+        int32_t own = 0, n_rec = 0;
         for (int attempt = 0; attempt < 2; ++attempt) {
             float dmin2 = __int_as_float(0x7f800000);
-            own_walk = 0;
-            for (int it = lane; it < L; it += 32) {
-                SplitItem item = s_items[w][cur][it];
-                const int32_t v = (int32_t)(item.node & ~kSub);
-                if (item.node & kSub) {
-                    int32_t ev = 0;
-                    subtree_walk<false>(a.nodes, v, x, self_node, thr0, k2, k2sh, 0.0f, item.val,
-                                        dmin2, ev);
-                    own_walk += ev;
-                } else {
-                    const float4 g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[v].g));
-                    const float d2 = dist2(x, g);
-                    item.val = attraction(g.w, d2, k2, k2sh);
-                    dmin2 = fminf(dmin2, d2);
-                }
-                s_items[w][cur][it].val = item.val;
-                ++my_steps;
-            }
-            __syncwarp();
-            // inclusive prefix in list order, FP64, sequential (S is its last entry)
-            if (lane == 0) {
-                double run = 0.0;
-                for (int it = 0; it < L; ++it) {
-                    run += (double)s_items[w][cur][it].val;
-                    s_pref[w][it] = run;
-                }
-            }
-            __syncwarp();
-            S = L > 0 ? s_pref[w][L - 1] : 0.0;
-            __syncwarp();
+            own = 0;
+            n_rec = split_walk(a, L, root, root_end, x, self_node, thr0, k2, k2sh, own, dmin2,
+                               my_steps, S);
             if (!(S < (double)kTiny)) break;
             // every term underflowed: redo with the exponents shifted by the nearest d^2
-            for (int o = 16; o; o >>= 1) dmin2 = fminf(dmin2, __shfl_xor_sync(0xffffffffu, dmin2, o));
+            for (int o = 16; o; o >>= 1)
+                dmin2 = fminf(dmin2, __shfl_xor_sync(0xffffffffu, dmin2, o));
             if (!(dmin2 < __int_as_float(0x7f800000))) break;
             k2sh = __fmul_rn(k2, dmin2);
+            __syncwarp();
         }
-        for (int o = 16; o; o >>= 1) own_walk += __shfl_xor_sync(0xffffffffu, own_walk, o);
-        own += own_walk;
+        own = warp_sum_i(own);
         if (lane == 0) my_evals += own;
 
         // ---- draws: the source's searches, one per lane
@@ -787,23 +820,12 @@ __global__ void __launch_bounds__(256) bh_split_kernel(SearchArgs a)
             if (S > 0.0) {
                 const uint32_t u = philox_x((uint32_t)i, a.step, (uint32_t)e << 8, 0u, a.seed);
                 const double tgt = (double)u * 2.3283064365386963e-10 * S;
-                int lo = 0, hi = L - 1; // first item whose inclusive prefix exceeds u * S
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (s_pref[w][mid] > tgt)
-                        hi = mid;
-                    else
-                        lo = mid + 1;
-                }
-                const SplitItem item = s_items[w][cur][lo];
-                int32_t k = (int32_t)(item.node & ~kSub);
-                if (item.node & kSub) {
-                    const double base = lo > 0 ? s_pref[w][lo - 1] : 0.0;
-                    float part, dm;
-                    int32_t ev;
-                    k = subtree_walk<true>(a.nodes, k, x, self_node, thr0, k2, k2sh,
-                                           (float)(tgt - base), part, dm, ev);
-                }
+                double base;
+                const int lo = split_locate(L, n_rec, tgt, base); // range holding u * S
+                const int32_t rb = L.b[L.ord[lo]];
+                const int32_t re = lo + 1 < n_rec ? L.b[L.ord[lo + 1]] : root_end;
+                const int32_t k = range_find(a.nodes, rb, re, x, self_node, thr0, k2, k2sh,
+                                             (float)(tgt - base));
                 result = restart_chain(a, k, x, self_node, thr0, k2, i, e, evals, draws,
                                        my_evals);
             }
@@ -816,7 +838,7 @@ __global__ void __launch_bounds__(256) bh_split_kernel(SearchArgs a)
                 a.diag_restarts[out] = draws > 0 ? draws - 1 : 0;
             }
         }
-        __syncwarp(); // the list buffers are reused by the next source
+        __syncwarp(); // the lists are reused by the next source
     }
     for (int off = 16; off; off >>= 1) {
         my_evals += __shfl_xor_sync(0xffffffffu, my_evals, off);
@@ -961,7 +983,11 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     void (*split)(SearchArgs) = a.net ? bh_split_kernel<true> : bh_split_kernel<false>;
     int per_sm = 0, per_sm_split = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0))) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_split, split, 256, 0)))
+    if ((e = cudaFuncSetAttribute(split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSplitSmem)))
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_split, split, 256,
+                                                           kSplitSmem)))
         return e;
     if (per_sm < 1) per_sm = 1;
     if (per_sm_split < 1) per_sm_split = 1;
@@ -970,14 +996,11 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     const int64_t warps = (int64_t)c->num_sms * per_sm * 8;
     auto cap = [](int64_t v) { return (int32_t)std::min<int64_t>(v, 1 << 30); };
     a.split_below = sg >= 3000 ? cap((int64_t)(sg - 3000) * 1024) : cap(warps * kSplitWaves);
-    a.split_min_nodes = sg == 0 ? kSplitMinNodes : 0;
-    a.num_nodes = c->d_i64 + I64_NODES;
-    a.lane_below = sg == 0 ? cap(warps * kLaneWaves) : 0;
     a.no8_below = sg == 0 ? cap(warps * kNo8Waves) : 0;
     // exactly one of the two kernels does the work (each reads the source count)
     kern<<<c->num_sms * per_sm, 256, 0, st>>>(a);
     note_launch();
-    split<<<c->num_sms * per_sm_split, 256, 0, st>>>(a);
+    split<<<c->num_sms * per_sm_split, 256, kSplitSmem, st>>>(a);
     note_launch();
     if (a.defer) {
         // regroup the deferred restarts by drawn node, then finish them

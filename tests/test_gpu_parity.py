@@ -136,14 +136,16 @@ def test_results_do_not_depend_on_search_group():
     a cumulative boundary, which the oracle's draw margin bounds."""
     net = workloads.gaussian_clusters(n=40000, clusters=6, side=3000, std=150, seed=33,
                                       sigma=300.0)
-    # 0, 1503 and 1300 pick the union kernel here (about 34k sources, above the default
-    # split threshold); 3000 never splits; 2 and 3999 always split
-    union = _requests_for_groups(net, (1, 8, 16, 32, 0, 1503, 1300, 3000))
+    # 3000 and 3001 pick the union kernel here (about 34k sources: never split, split
+    # below 1024 sources); 2 and 3999 always split, and so do the defaults 0, 1503 and
+    # 1300 (34k sources are below their split threshold)
+    union = _requests_for_groups(net, (1, 8, 16, 32, 3000, 3001))
     for other in union[1:]:
         for a, b in zip(union[0], other):
             assert np.array_equal(a, b)
-    split = _requests_for_groups(net, (2, 3999))
-    assert all(np.array_equal(x, y) for x, y in zip(split[0], split[1]))
+    split = _requests_for_groups(net, (2, 3999, 0, 1503, 1300))
+    for other in split[1:]:
+        assert all(np.array_equal(x, y) for x, y in zip(split[0], other))
     ut, ua, uls, uev = union[0]
     st, sa, sls, sev = split[0]
     fin = np.isfinite(uls)
