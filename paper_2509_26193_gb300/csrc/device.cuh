@@ -69,6 +69,18 @@ struct __align__(32) Node {
     NodeTopo t;
 };
 
+// A whole node (32 bytes, 32-byte aligned) in one 256-bit read-only load
+// (PTX ld.global.nc.v8.f32, sm_100 and later): geometry and escape/shift.
+__device__ __forceinline__ void load_node(const Node *n, float4 &g, int2 &t)
+{
+    float v0, v1, v2, v3, v4, v5, v6, v7;
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(v0), "=f"(v1), "=f"(v2), "=f"(v3), "=f"(v4), "=f"(v5), "=f"(v6), "=f"(v7)
+        : "l"(n));
+    g = make_float4(v0, v1, v2, v3);
+    t = make_int2(__float_as_int(v4), __float_as_int(v5));
+}
+
 constexpr int kMaxDepth = 10;
 
 // Number of leading octal digits (octree levels) two Morton codes share; 10 when equal.

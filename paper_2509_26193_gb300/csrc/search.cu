@@ -586,8 +586,9 @@ __device__ __forceinline__ int32_t range_find(const Node *__restrict__ nodes, in
     int32_t p = b, pick = -1;
     float cum = 0.0f, comp = 0.0f;
     while (p < e) {
-        const float4 g = __ldg(reinterpret_cast<const float4 *>(&nodes[p].g));
-        const int2 t = __ldg(reinterpret_cast<const int2 *>(&nodes[p].t));
+        float4 g;
+        int2 t;
+        load_node(&nodes[p], g, t);
         const float d2 = dist2(x, g);
         const bool has = g.w > 0.0f;
         const bool acc = has && (__float_as_uint(d2) + (uint32_t)t.y > thr0);
@@ -674,8 +675,9 @@ __device__ __forceinline__ int split_walk(const SearchArgs &a, SplitLists &L, in
         bool split = false;
         int32_t rest = 0;
         if (busy) {
-            const float4 g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[p].g));
-            const int2 t = __ldg(reinterpret_cast<const int2 *>(&a.nodes[p].t));
+            float4 g;
+            int2 t;
+            load_node(&a.nodes[p], g, t);
             const float d2 = dist2(x, g);
             const bool has = g.w > 0.0f;
             const bool acc = has && (__float_as_uint(d2) + (uint32_t)t.y > thr0);
