@@ -45,7 +45,7 @@ typedef enum {
     RELEARN_ERR_CUDA = 2,        /* a CUDA runtime call failed; see relearn_last_error */
     RELEARN_ERR_OOM = 3,         /* device allocation failed in relearn_create */
     RELEARN_ERR_CAPACITY = 4,    /* searches or synapses exceeded the context's capacity */
-    RELEARN_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+    RELEARN_ERR_TIMEOUT = 5,     /* a bounded device wait gave up (bottom-up update) */
     RELEARN_ERR_STATE = 6        /* call out of order (e.g. update before build) */
 } relearn_status;
 

@@ -79,7 +79,7 @@ void free_all(relearn_ctx *c)
         (void **)&c->d_codes_alt, (void **)&c->d_perm,      (void **)&c->d_perm_alt,
         (void **)&c->d_pos,      (void **)&c->d_posq,       (void **)&c->d_mask,       (void **)&c->d_base,
         (void **)&c->d_nodes,    (void **)&c->d_parent,     (void **)&c->d_nsize,
-        (void **)&c->d_leaf,     (void **)&c->d_acc,
+        (void **)&c->d_leaf,     (void **)&c->d_acc,        (void **)&c->d_lb,
         (void **)&c->d_cnt,      (void **)&c->d_act_off,    (void **)&c->d_qoff_o,
         (void **)&c->d_act_src,  (void **)&c->d_req_src,    (void **)&c->d_req_elem,
         (void **)&c->d_req_tgt,  (void **)&c->d_req_acc,    (void **)&c->d_req_prio,
@@ -219,7 +219,8 @@ relearn_status relearn_create_batched(relearn_ctx **out, int device, int64_t max
     A(d_parent, M);
     A(d_nsize, M);
     A(d_leaf, N);
-    A(d_acc, 4 * M);
+    A(d_acc, 4 * M + 8 * (N / 1024 + 2)); // L4 prefix (n + 1) and 2 per prefix tile
+    A(d_lb, N / 1024 + 3);
     A(d_cnt, N + 1);
     A(d_act_off, N + 1);
     A(d_qoff_o, N + 1);

@@ -73,12 +73,13 @@ struct __align__(32) Node {
 // (PTX ld.global.nc.v8.f32, sm_100 and later): geometry and escape/shift.
 __device__ __forceinline__ void load_node(const Node *n, float4 &g, int2 &t)
 {
-    float v0, v1, v2, v3, v4, v5, v6, v7;
+    float v[8];
     asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(v0), "=f"(v1), "=f"(v2), "=f"(v3), "=f"(v4), "=f"(v5), "=f"(v6), "=f"(v7)
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+          "=f"(v[7])
         : "l"(n));
-    g = make_float4(v0, v1, v2, v3);
-    t = make_int2(__float_as_int(v4), __float_as_int(v5));
+    g = make_float4(v[0], v[1], v[2], v[3]);
+    t = make_int2(__float_as_int(v[4]), __float_as_int(v[5]));
 }
 
 constexpr int kMaxDepth = 10;

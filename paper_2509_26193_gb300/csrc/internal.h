@@ -81,7 +81,8 @@ struct relearn_ctx {
     int32_t *d_parent = nullptr;                         // [max_nodes] (get_tree)
     int32_t *d_nsize = nullptr;                          // [max_nodes] neurons in the node's cell
     int32_t *d_leaf = nullptr;                           // [n] leaf node of each position
-    double *d_acc = nullptr;  // [4 * max_nodes] FP64 prefix sums and block sums (reduce)
+    double *d_acc = nullptr;  // bottom-up update: int64 x 4 prefix and tile sums
+    int32_t *d_lb = nullptr;  // [max_neurons / 1024 + 3] single-pass prefix tile states
 
     // ---- queries and requests (per update)
     int32_t *d_cnt = nullptr;       // [n + 1] scratch counts

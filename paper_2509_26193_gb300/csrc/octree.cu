@@ -455,54 +455,103 @@ __device__ __forceinline__ L4 leaf_weight(Node *nodes, const int32_t *leaf_of,
     return L4{lc, lc * q.x, lc * q.y, lc * q.z};
 }
 
+// Single pass over the leaves (decoupled look-back): each block takes the next
+// tile by ticket, writes the tile's leaves and sums their weights, publishes the
+// tile sum, then its first warp reads the states of the 32 preceding tiles at
+// once and adds their published sums back to the nearest one that has published
+// its inclusive prefix (further windows of 32 if none has), and the block
+// publishes its own inclusive prefix. A block only waits for tiles with smaller
+// tickets, which are already running or done and publish their sums before they
+// wait themselves, so every wait ends; each is still bounded (kLbSpin rounds,
+// then RELEARN_ERR_TIMEOUT in *status and no block waits any more).
+// lb[0]: ticket counter, lb[1]: abort flag, lb[2 + t]: state of tile t; all zero
+// at launch.
+constexpr int32_t kLbAgg = 1, kLbInc = 2;
+constexpr int kLbSpin = 1 << 16;
+
+__device__ __forceinline__ L4 l4_load_volatile(const L4 *p)
+{
+    const volatile long long *q = reinterpret_cast<const volatile long long *>(p);
+    return L4{q[0], q[1], q[2], q[3]};
+}
+
+__device__ __forceinline__ L4 l4_warp_sum(L4 v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1)
+        v = l4_add(v, L4{__shfl_xor_sync(0xffffffffu, v.c, o), __shfl_xor_sync(0xffffffffu, v.x, o),
+                         __shfl_xor_sync(0xffffffffu, v.y, o), __shfl_xor_sync(0xffffffffu, v.z, o)});
+    return v;
+}
+
 __global__ void __launch_bounds__(256)
-    reduce_sums_kernel(Node *nodes, const int32_t *__restrict__ leaf_of,
+    reduce_scan_kernel(Node *nodes, const int32_t *__restrict__ leaf_of,
                        const int32_t *__restrict__ perm, const float4 *__restrict__ pos,
                        const int4 *__restrict__ posq, const int32_t *__restrict__ vac_de,
-                       int64_t n, L4 *__restrict__ block_sums)
+                       int64_t n, int64_t nb, int32_t *lb, L4 *agg, L4 *inc,
+                       L4 *__restrict__ P, int32_t *status)
 {
-    const int64_t base = (int64_t)blockIdx.x * kRedTile + (int64_t)threadIdx.x * kRedItems;
-    L4 acc{0, 0, 0, 0};
-    for (int k = 0; k < kRedItems; ++k)
-        if (base + k < n)
-            acc = l4_add(acc, leaf_weight(nodes, leaf_of, perm, pos, posq, vac_de, base + k, true));
-    L4 tot;
-    l4_block_inclusive(acc, &tot);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(256) reduce_spine_kernel(L4 *block_sums, int64_t nb, L4 *P,
-                                                           int64_t n)
-{
-    L4 carry{0, 0, 0, 0};
-    for (int64_t c0 = 0; c0 < nb; c0 += 256) {
-        const int64_t i = c0 + threadIdx.x;
-        const L4 v = i < nb ? block_sums[i] : L4{0, 0, 0, 0};
-        L4 tot;
-        const L4 inc = l4_block_inclusive(v, &tot);
-        if (i < nb) block_sums[i] = l4_add(carry, l4_sub(inc, v));
-        carry = l4_add(carry, tot);
-    }
-    if (threadIdx.x == 0) P[n] = carry;
-}
-
-__global__ void __launch_bounds__(256)
-    reduce_prefix_kernel(Node *nodes, const int32_t *__restrict__ leaf_of,
-                         const int32_t *__restrict__ perm, const float4 *__restrict__ pos,
-                         const int4 *__restrict__ posq, const int32_t *__restrict__ vac_de,
-                         int64_t n, const L4 *__restrict__ block_sums, L4 *__restrict__ P)
-{
-    const int64_t base = (int64_t)blockIdx.x * kRedTile + (int64_t)threadIdx.x * kRedItems;
+    __shared__ int32_t s_tile;
+    __shared__ L4 s_prefix;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&lb[0], 1);
+    __syncthreads();
+    const int64_t t = s_tile;
+    const int64_t base = t * kRedTile + (int64_t)threadIdx.x * kRedItems;
     L4 w[kRedItems];
     L4 acc{0, 0, 0, 0};
     for (int k = 0; k < kRedItems; ++k) {
-        w[k] = base + k < n ? leaf_weight(nodes, leaf_of, perm, pos, posq, vac_de, base + k, false)
+        w[k] = base + k < n ? leaf_weight(nodes, leaf_of, perm, pos, posq, vac_de, base + k, true)
                             : L4{0, 0, 0, 0};
         acc = l4_add(acc, w[k]);
     }
     L4 tot;
-    const L4 inc = l4_block_inclusive(acc, &tot);
-    L4 run = l4_add(block_sums[blockIdx.x], l4_sub(inc, acc));
+    const L4 incl = l4_block_inclusive(acc, &tot);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        volatile int32_t *state = lb + 2;
+        L4 prefix{0, 0, 0, 0};
+        if (t > 0) {
+            if (lane == 0) {
+                agg[t] = tot;
+                __threadfence();
+                atomicExch(&lb[2 + t], kLbAgg);
+            }
+            for (int64_t j0 = t - 1;; j0 -= 32) {
+                const int64_t j = j0 - lane; // this lane's predecessor (j < 0: prefix zero)
+                int32_t f = j < 0 ? kLbInc : 0;
+                bool ready = false;
+                for (int spin = 0; spin < kLbSpin; ++spin) {
+                    if (j >= 0) f = state[j];
+                    ready = __all_sync(0xffffffffu, f != 0);
+                    if (ready || *(volatile int32_t *)&lb[1]) break;
+                }
+                if (!ready) { // gave up (or another block did): report, stop waiting
+                    if (lane == 0) {
+                        set_status(status, RELEARN_ERR_TIMEOUT);
+                        atomicExch(&lb[1], 1);
+                    }
+                    break;
+                }
+                __threadfence();
+                const uint32_t incm = __ballot_sync(0xffffffffu, f == kLbInc);
+                const int stop = incm ? __ffs(incm) - 1 : 32; // nearest inclusive prefix
+                L4 v{0, 0, 0, 0};
+                if (j >= 0 && lane < stop) v = l4_load_volatile(&agg[j]);
+                if (j >= 0 && lane == stop) v = l4_load_volatile(&inc[j]);
+                prefix = l4_add(prefix, l4_warp_sum(v));
+                if (incm) break;
+            }
+        }
+        if (lane == 0) {
+            inc[t] = l4_add(prefix, tot);
+            __threadfence();
+            atomicExch(&lb[2 + t], kLbInc);
+            s_prefix = prefix;
+            if (t == nb - 1) P[n] = l4_add(prefix, tot);
+        }
+    }
+    __syncthreads();
+    L4 run = l4_add(s_prefix, l4_sub(incl, acc));
     for (int k = 0; k < kRedItems; ++k) {
         if (base + k < n) P[base + k] = run;
         run = l4_add(run, w[k]);
@@ -615,15 +664,14 @@ cudaError_t octree_reduce(relearn_ctx *c, const int32_t *vac_de, cudaStream_t st
 {
     const int64_t n = c->n;
     const int64_t nb = (n + kRedTile - 1) / kRedTile;
-    L4 *P = reinterpret_cast<L4 *>(c->d_acc);      // n + 1 prefix entries
-    L4 *bsum = P + (n + 1);                          // nb block sums (d_acc holds 2n + 1)
-    reduce_sums_kernel<<<(unsigned)nb, 256, 0, st>>>(c->d_nodes, c->d_leaf, c->d_perm, c->d_pos,
-                                                      c->d_posq, vac_de, n, bsum);
-    note_launch();
-    reduce_spine_kernel<<<1, 256, 0, st>>>(bsum, nb, P, n);
-    note_launch();
-    reduce_prefix_kernel<<<(unsigned)nb, 256, 0, st>>>(c->d_nodes, c->d_leaf, c->d_perm,
-                                                        c->d_pos, c->d_posq, vac_de, n, bsum, P);
+    L4 *P = reinterpret_cast<L4 *>(c->d_acc); // n + 1 prefix entries
+    L4 *agg = P + (n + 1);                      // nb tile sums, nb inclusive prefixes
+    L4 *inc = agg + nb;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->d_lb, 0, (size_t)(nb + 2) * sizeof(int32_t), st))) return e;
+    reduce_scan_kernel<<<(unsigned)nb, 256, 0, st>>>(c->d_nodes, c->d_leaf, c->d_perm, c->d_pos,
+                                                      c->d_posq, vac_de, n, nb, c->d_lb, agg,
+                                                      inc, P, c->d_status);
     note_launch();
     reduce_nodes_kernel<<<grid_for(c->max_nodes, 256, c->num_sms), 256, 0, st>>>(
         c->d_nodes, c->d_nsize, c->d_i64 + I64_NODES, P, c->num_nets > 1 ? c->d_net : nullptr,

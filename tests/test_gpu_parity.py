@@ -85,11 +85,12 @@ def _oracle_searches(net, tree, step, theta, qi=None, qe=None):
     return qi, qe, tree.search_batch(net.sigma, theta, net.seed, step, qi, qe, threads=8)
 
 
-@pytest.mark.parametrize("group", [0, 2])
+@pytest.mark.parametrize("group", [0, 2, 1, 32])
 @pytest.mark.parametrize("theta", [0.3, 0.0, 0.5, 0.2])
 def test_search_matches_oracle_4096(theta, group):
-    """group 0 is the default (the union kernel for a tree this small), 2 forces the
-    split kernel (one warp per source)."""
+    """group 0 is the default (the split kernel, one warp per source, for an update
+    this small), 2 forces the split kernel, 1 and 32 the union kernel (every lane
+    alone; unions of 32 sources)."""
     from paper_2509_26193_gb300 import relearn as R
     net = workloads.uniform_cube(n=4096, seed=1)
     g = GpuNet(net)
