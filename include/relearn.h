@@ -68,11 +68,11 @@ typedef struct relearn_ctx relearn_ctx;
  *             1, 8, 16 or 32 = a fixed width;
  *             2 = one source per warp, its frontier walk shared out over the 32 lanes;
  *             0 = the default: one source per warp when the update has at most 9 sources
- *             per resident warp of the union kernel, else chosen per warp from how close
- *             its sources are;
- *             1000 + 100 * d32 + d8 (d32, d8 = 0..10) = chosen per warp: 32 together when
- *             they share a cell of depth >= d32, else 8 together when they share a cell of
- *             depth >= d8, else one by one;
+ *             per resident warp of the union kernel, else unions chosen per warp: its 32
+ *             sources (Morton order) cut at the boundaries of depth-4 cells, one union
+ *             per piece;
+ *             1000 + 100 * d + r (d = 0..10, r = 0..10, r unused) = the default with the
+ *             pieces cut at the boundaries of depth-d cells;
  *             3000 + f (f = 0..999) = the default with one source per warp for updates of
  *             at most f * 1024 sources.
  *   net_sigma, net_theta  device float[num_networks] or NULL (updates only): per-network

@@ -17,9 +17,9 @@ from __future__ import annotations
 
 from typing import Callable, Dict, Iterable, Tuple
 
-# 0 = the library's default thresholds; 1 / 8 / 32 = one fixed width for every
-# warp; 1000 + 100 * d32 + d8 = per-warp choice with thresholds d32 and d8.
-DEFAULT_CANDIDATES = (0, 1, 8, 32, 1302, 1303, 1402, 1403, 1503, 1504, 1604)
+# 0 = the library's default; 1 / 8 / 32 = one fixed width for every warp;
+# 1000 + 100 * d = per-warp unions cut at the boundaries of depth-d cells.
+DEFAULT_CANDIDATES = (0, 1, 8, 32, 1200, 1300, 1500, 1600)
 
 
 def tune(trial: Callable[[int], float], candidates: Iterable[int] = DEFAULT_CANDIDATES,

@@ -41,20 +41,18 @@ namespace {
 constexpr int kCkStride = 128; // warp steps between checkpoints
 constexpr int kMaxCk = 128;    // checkpoints kept per lane (later steps reuse the last one)
 constexpr float kTiny = 8.673617e-19f; // 2^-60
-// Walk width per warp (see bh_search_kernel): the 32 sources of a warp share one walk
-// when they lie in one cell of depth >= kSpreadDepth, else groups of 8 do when each of
-// those fits such a cell, else every lane walks alone.
+// Walks per warp (see bh_search_kernel): the warp's 32 sources are cut into pieces
+// at the boundaries of cells of depth kSpreadDepth, and each piece walks one union
+// (update 0 of the 2^20-neuron clustered network: 73 % of warps form one piece; the
+// others used to walk lane by lane or in unions of 8).
 constexpr int kSpreadDepth = 4;
-constexpr int kSpreadDepth8 = 3;
 // The default also looks at how many sources the update has, per resident warp of
 // the union kernel (W = 7,296 on 152 SMs). Per-update sweeps on the 2^20-neuron
 // clustered network (ten successive updates, 907k down to 2.4k sources): with at
 // most kSplitWaves * W sources the split kernel (one warp per source) wins (61.8k
 // sources: 1.67 ms against 1.84 ms; 162k: 4.73 ms against 2.46 ms), on small trees
-// as well (4096-neuron cube, 4096 sources: 0.10 ms against 0.46 ms); below
-// kNo8Waves * W unions of 8 lose to lanes walking alone.
+// as well (4096-neuron cube, 4096 sources: 0.10 ms against 0.46 ms).
 constexpr int kSplitWaves = 9;
-constexpr int kNo8Waves = 40;
 
 // A node of depth d is accepted iff d^2 > thr0 / 4^d, thr0 = (root length / theta)^2
 // rounded to FP32 (see NodeTopo::shift). theta = 0 accepts no inner node.
@@ -166,9 +164,7 @@ struct SearchArgs {
     uint32_t step;
     int forced_group; // 0 = choose per warp; 1, 8, 16, 32 = union width; 2 = split
     int spread_depth;  // a union of 32 needs all sources in one cell this deep
-    int spread_depth8; // else a union of 8 needs its sources in one cell this deep
     int32_t split_below; // with forced_group 0: split kernel for at most this many sources
-    int32_t no8_below;   // default only: no unions of 8 below this many sources
     // deferred restarts (RELEARN_FLAG_REGROUP): searches whose first draw is an inner
     // node are queued here and finished after a sort by that node (subtree order)
     int defer;
@@ -333,10 +329,11 @@ __device__ __forceinline__ void enqueue_restart(const SearchArgs &a, int32_t k, 
     }
 }
 
-// G = lanes per union walk (1, 8, 16 or 32), chosen per warp task from the spread of
-// its 32 sources (a union is only worth walking when its sources are close: far-apart
-// sources share few nodes and most lanes would idle). A warp runs 32 / G independent
-// walks, 32 / G node loads in flight per step. Results do not depend on G.
+// A warp's sources walk in unions chosen per warp task from where they lie (a union
+// is only worth walking when its sources are close: far-apart sources share few
+// nodes and most lanes would idle), or in fixed groups of G = 1, 8, 16 or 32 lanes
+// when search_group forces a width. A warp runs one walk per union, one node load
+// in flight per union and step. Results do not depend on the grouping.
 #ifndef RELEARN_SEARCH_MIN_BLOCKS
 #define RELEARN_SEARCH_MIN_BLOCKS 6 // 40 registers: 6 blocks of 256 threads per SM
 #endif
@@ -391,22 +388,30 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
             mixed8 = __any_sync(0xffffffffu, nf != nl);
         }
 
-        // ---- walk width: Morton codes are sorted, so the first and last code of a
-        // range bound the cell that holds all of it; a union never spans two networks
+        // ---- walks: the warp's 32 sources (Morton order) are cut wherever two
+        // neighbours do not share a cell of depth spread_depth (or a network); each
+        // piece walks one union. Codes are sorted, so a piece whose neighbours all
+        // share that cell lies in one such cell. One piece: a single walk (G = 32).
         int G = a.forced_group;
+        uint32_t gmask = 0xffffffffu;
+        int seg_first = 0; // first lane of this lane's walk
         if (G == 0) {
             uint32_t code = live ? a.codes[s] : 0u;
             code = __shfl_sync(0xffffffffu, code, live ? lane : last);
-            const uint32_t c0 = __shfl_sync(0xffffffffu, code, 0);
-            const uint32_t c31 = __shfl_sync(0xffffffffu, code, 31);
-            if (n0 == n31 && morton_common_digits(c0, c31) >= a.spread_depth) {
-                G = 32;
-            } else {
-                const uint32_t f = __shfl_sync(0xffffffffu, code, lane & ~7);
-                const uint32_t l = __shfl_sync(0xffffffffu, code, lane | 7);
-                const int cp8 = __reduce_min_sync(0xffffffffu, morton_common_digits(f, l));
-                G = !mixed8 && cp8 >= a.spread_depth8 && A >= a.no8_below ? 8 : 1;
+            const uint32_t nxt = __shfl_down_sync(0xffffffffu, code, 1);
+            bool cut = lane < 31 && morton_common_digits(code, nxt) < a.spread_depth;
+            if constexpr (kBatched) {
+                const int32_t nn = __shfl_down_sync(0xffffffffu, net, 1);
+                cut = cut || (lane < 31 && nn != net);
             }
+            const uint32_t cuts = __ballot_sync(0xffffffffu, cut); // bit i: cut after lane i
+            const uint32_t below = cuts & ((1u << lane) - 1u);
+            seg_first = below ? 32 - __clz(below) : 0;
+            const uint32_t from = cuts >> lane;
+            const int seg_last = from ? lane + __ffs(from) - 1 : 31;
+            gmask = (seg_last == 31 ? 0xffffffffu : ((1u << (seg_last + 1)) - 1u)) &
+                    ~((1u << seg_first) - 1u);
+            G = cuts ? 0 : 32;
         } else if (kBatched && G > 1 && n0 != n31) {
             // a fixed width whose groups would span networks: the widest that does not
             const int32_t nh = __shfl_sync(0xffffffffu, net, lane & ~15);
@@ -416,8 +421,10 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                                                                                 : G;
             if (G == 8 && mixed8) G = 1;
         }
-        const uint32_t gmask =
-            G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+        if (a.forced_group != 0) {
+            gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+            seg_first = lane & ~(G - 1);
+        }
 
         // ---- pass 1: union of the G root frontiers of this lane's group
         float k2sh = 0.0f;
@@ -483,7 +490,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                     if (run) p = down ? p + 1 : max(t.x, p + 1);
                 }
             }
-            if ((lane & (G - 1)) == 0) my_steps += steps; // one count per walk
+            if (lane == seg_first) my_steps += steps; // one count per walk
             S = (double)cum - (double)comp;
             // every term underflowed: redo with the exponents shifted by the nearest d^2
             const bool redo = live && S < (double)kTiny;
@@ -974,13 +981,12 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     a.rq_count = c->d_i32 + I32_RQ;
     if (a.defer && (e = cudaMemsetAsync(a.rq_count, 0, sizeof(int32_t), st))) return e;
     // search_group: 0 = per-warp choice, 1/8/16/32 = fixed width, 2 = split kernel,
-    // 1000 + 100 * d32 + d8 = per-warp choice with spread depths d32, d8 (tuning),
+    // 1000 + 100 * d + r = per-warp pieces cut at depth-d cells (tuning; r unused),
     // 3000 + f = per-warp choice, split kernel for at most f * 1024 sources (tuning)
     const uint32_t sg = p.search_group;
     a.forced_group = sg < 1000 ? (int)sg : 0;
     const bool depths = sg >= 1000 && sg < 3000;
     a.spread_depth = depths ? (int)((sg - 1000) / 100) : kSpreadDepth;
-    a.spread_depth8 = depths ? (int)((sg - 1000) % 100) : kSpreadDepth8;
     void (*kern)(SearchArgs) = a.net ? bh_search_kernel<true> : bh_search_kernel<false>;
     void (*split)(SearchArgs) = a.net ? bh_split_kernel<true> : bh_split_kernel<false>;
     int per_sm = 0, per_sm_split = 0;
@@ -998,7 +1004,6 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     const int64_t warps = (int64_t)c->num_sms * per_sm * 8;
     auto cap = [](int64_t v) { return (int32_t)std::min<int64_t>(v, 1 << 30); };
     a.split_below = sg >= 3000 ? cap((int64_t)(sg - 3000) * 1024) : cap(warps * kSplitWaves);
-    a.no8_below = sg == 0 ? cap(warps * kNo8Waves) : 0;
     // exactly one of the two kernels does the work (each reads the source count)
     kern<<<c->num_sms * per_sm, 256, 0, st>>>(a);
     note_launch();
