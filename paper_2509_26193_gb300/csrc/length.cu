@@ -11,8 +11,9 @@
 //   dl_i/dc_k   = q_ik r_ik (2 (d_ik - l_i) / sigma^2 - 1 / d_ik),  r = x_i - c_k,
 //   dl_i/dx_i   = -sum_k dl_i/dc_k,   dc_k/dx_j = w_j / N_k  (w = vac_de).
 //
-// Forward: one walk of each root frontier (the search kernel's warp-union walk:
-// 32 sources in one cell walk the union of their frontiers, else lane by lane),
+// Forward: one walk of each root frontier (the search kernel's warp-union walk: the
+// warp's 32 sources, cut at the boundaries of depth-4 cells, walk one union per
+// piece),
 // FP32 attractions with Kahan-compensated sums; S, l and Dbar formed in FP64 and
 // kept per source with the exponent shift. Backward: the same walk again,
 // recomputing every attraction (nothing per candidate is stored), accumulating
@@ -30,7 +31,7 @@ namespace rl {
 namespace {
 
 constexpr float kTinyL = 8.673617e-19f; // 2^-60: below this S is redone with a shift
-constexpr int kUnionDepth = 4;          // 32 sources in one cell this deep share a walk
+constexpr int kUnionDepth = 4;          // sources in one cell this deep share a walk
 
 struct LenArgs {
     const Node *__restrict__ nodes;
@@ -189,15 +190,54 @@ __global__ void __launch_bounds__(256, 6) length_kernel(LenArgs a)
             on_src = live && s.invS > 0.0f;
             s.w = on_src ? (float)((double)a.vac_ax[i] * wscale) : 0.0f;
         }
-        // union walk when the 32 sources share a cell of depth >= kUnionDepth
+        // the 32 sources (Morton order) are cut wherever two neighbours do not share a
+        // cell of depth kUnionDepth; each piece walks one union (one piece: uni)
         const int last = min(A - 1 - nb, 31);
         uint32_t code = live ? a.codes[sp] : 0u;
         code = __shfl_sync(0xffffffffu, code, live ? lane : last);
-        const bool uni = morton_common_digits(__shfl_sync(0xffffffffu, code, 0),
-                                              __shfl_sync(0xffffffffu, code, 31)) >= kUnionDepth;
+        const uint32_t nxt = __shfl_down_sync(0xffffffffu, code, 1);
+        const uint32_t cuts = __ballot_sync(
+            0xffffffffu, lane < 31 && morton_common_digits(code, nxt) < kUnionDepth);
+        const bool uni = cuts == 0;
         Fwd f;
         Bwd b;
-        if (uni) {
+        if (!uni) {
+            const uint32_t below = cuts & ((1u << lane) - 1u);
+            const int first = below ? 32 - __clz(below) : 0;
+            const uint32_t from = cuts >> lane;
+            const int lastl = from ? lane + __ffs(from) - 1 : 31;
+            const uint32_t gmask = (lastl == 31 ? 0xffffffffu : ((1u << (lastl + 1)) - 1u)) &
+                                   ~((1u << first) - 1u);
+            int32_t p = 1, skip = on_src ? 0 : 0x7fffffff;
+            while (__any_sync(0xffffffffu, p < root_end)) {
+                const bool run = p < root_end; // uniform within the piece
+                float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+                int2 t = make_int2(p + 1, 0);
+                if (run) {
+                    g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[p].g));
+                    t = __ldg(reinterpret_cast<const int2 *>(&a.nodes[p].t));
+                }
+                const float rx = __fsub_rn(s.x.x, g.x), ry = __fsub_rn(s.x.y, g.y),
+                            rz = __fsub_rn(s.x.z, g.z);
+                const float D = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, __fmul_rn(rz, rz)));
+                const bool on = run && p >= skip && g.w > 0.0f;
+                const bool pass = __float_as_uint(D) + (uint32_t)t.y > thr0;
+                const bool take = on && pass && p != s.self;
+                if (on && pass) skip = t.x;
+                my_evals += take ? 1 : 0;
+                if constexpr (!kBack) {
+                    if (take) fwd_visit(f, g.w, D, k2, 0.0f);
+                } else {
+                    if (take) {
+                        float ox, oy, oz;
+                        bwd_visit(b, s, g.w, rx, ry, rz, D, k2, two_s2, ox, oy, oz);
+                        add_node(a.G, p, ox, oy, oz);
+                    }
+                }
+                const uint32_t down = __ballot_sync(0xffffffffu, on && !pass) & gmask;
+                if (run) p = down ? p + 1 : max(t.x, p + 1);
+            }
+        } else {
             int32_t p = 1, skip = on_src ? 0 : 0x7fffffff;
             while (p < root_end) {
                 const float4 g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[p].g));
@@ -221,9 +261,6 @@ __global__ void __launch_bounds__(256, 6) length_kernel(LenArgs a)
                 }
                 p = __any_sync(0xffffffffu, on && !pass) ? p + 1 : max(t.x, p + 1);
             }
-        } else if (on_src) {
-            my_evals += lane_walk<kBack>(a, s, root_end, thr0, k2, kBack ? s.k2sh : 0.0f, two_s2,
-                                         f, b);
         }
         if constexpr (!kBack) {
             if (!live) continue;
