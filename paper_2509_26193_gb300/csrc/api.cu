@@ -136,9 +136,11 @@ relearn_status read_status(relearn_ctx *c)
     if (st != 0) {
         cudaMemset(c->d_status, 0, sizeof(int32_t));
         return fail(c, (relearn_status)st,
-                    st == RELEARN_ERR_CAPACITY ? "capacity exceeded on the device (searches or "
-                                                 "synapses); nothing was applied"
-                                               : "device-side error");
+                    st == RELEARN_ERR_CAPACITY  ? "capacity exceeded on the device (searches or "
+                                                  "synapses); nothing was applied"
+                    : st == RELEARN_ERR_TIMEOUT ? "a bounded wait of the bottom-up update gave "
+                                                  "up; nothing was applied"
+                                                : "device-side error; nothing was applied");
     }
     return RELEARN_OK;
 }
@@ -468,6 +470,13 @@ relearn_status relearn_update_connectivity_typed(relearn_ctx *c, const relearn_p
         }
     }
     if (stats) *stats = sum;
+    return RELEARN_OK;
+}
+
+relearn_status relearn_debug_stall_reduce(relearn_ctx *c, int64_t tile)
+{
+    if (!c) return RELEARN_ERR_INVALID_ARG;
+    c->debug_stall_tile = tile < 0 ? -1 : tile;
     return RELEARN_OK;
 }
 

@@ -83,6 +83,7 @@ struct relearn_ctx {
     int32_t *d_leaf = nullptr;                           // [n] leaf node of each position
     double *d_acc = nullptr;  // bottom-up update: int64 x 4 prefix and tile sums
     int32_t *d_lb = nullptr;  // [max_neurons / 1024 + 3] single-pass prefix tile states
+    int64_t debug_stall_tile = -1; // relearn_debug_stall_reduce: next update only
 
     // ---- queries and requests (per update)
     int32_t *d_cnt = nullptr;       // [n + 1] scratch counts

@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(256)
                        const int32_t *__restrict__ perm, const float4 *__restrict__ pos,
                        const int4 *__restrict__ posq, const int32_t *__restrict__ vac_de,
                        int64_t n, int64_t nb, int32_t *lb, L4 *agg, L4 *inc,
-                       L4 *__restrict__ P, int32_t *status)
+                       L4 *__restrict__ P, int32_t *status, int64_t stall_tile)
 {
     __shared__ int32_t s_tile;
     __shared__ L4 s_prefix;
@@ -510,8 +510,10 @@ __global__ void __launch_bounds__(256)
         const int lane = threadIdx.x;
         volatile int32_t *state = lb + 2;
         L4 prefix{0, 0, 0, 0};
+        // stall_tile (a test of the bounded waits): that tile never publishes
+        const bool publish = t != stall_tile;
         if (t > 0) {
-            if (lane == 0) {
+            if (lane == 0 && publish) {
                 agg[t] = tot;
                 __threadfence();
                 atomicExch(&lb[2 + t], kLbAgg);
@@ -543,9 +545,11 @@ __global__ void __launch_bounds__(256)
             }
         }
         if (lane == 0) {
-            inc[t] = l4_add(prefix, tot);
-            __threadfence();
-            atomicExch(&lb[2 + t], kLbInc);
+            if (publish) {
+                inc[t] = l4_add(prefix, tot);
+                __threadfence();
+                atomicExch(&lb[2 + t], kLbInc);
+            }
             s_prefix = prefix;
             if (t == nb - 1) P[n] = l4_add(prefix, tot);
         }
@@ -671,7 +675,9 @@ cudaError_t octree_reduce(relearn_ctx *c, const int32_t *vac_de, cudaStream_t st
     if ((e = cudaMemsetAsync(c->d_lb, 0, (size_t)(nb + 2) * sizeof(int32_t), st))) return e;
     reduce_scan_kernel<<<(unsigned)nb, 256, 0, st>>>(c->d_nodes, c->d_leaf, c->d_perm, c->d_pos,
                                                       c->d_posq, vac_de, n, nb, c->d_lb, agg,
-                                                      inc, P, c->d_status);
+                                                      inc, P, c->d_status,
+                                                      c->debug_stall_tile);
+    c->debug_stall_tile = -1; // one update only
     note_launch();
     reduce_nodes_kernel<<<grid_for(c->max_nodes, 256, c->num_sms), 256, 0, st>>>(
         c->d_nodes, c->d_nsize, c->d_i64 + I64_NODES, P, c->num_nets > 1 ? c->d_net : nullptr,

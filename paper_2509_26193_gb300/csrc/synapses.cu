@@ -124,8 +124,9 @@ __global__ void apply_check_kernel(const int64_t *d_formed, int32_t *d_nsyn, int
                                    int64_t max_synapses, int32_t *status, int64_t *d_formed_out)
 {
     int64_t f = *d_formed;
-    if ((int64_t)*d_nsyn + f > max_synapses) {
-        set_status(status, RELEARN_ERR_CAPACITY);
+    const bool failed = *(volatile int32_t *)status != 0; // an earlier kernel reported an error
+    if (failed || (int64_t)*d_nsyn + f > max_synapses) {
+        if (!failed) set_status(status, RELEARN_ERR_CAPACITY);
         *d_new = -1;
         *d_formed_out = 0;
     } else {

@@ -347,6 +347,35 @@ def test_capacity_overflow_is_reported_and_nothing_applied():
     g.close()
 
 
+def test_bounded_wait_timeout_is_reported_and_nothing_applied():
+    """The bottom-up update's single-pass prefix waits, bounded, for the sums of the
+    tiles before it. With one tile made never to publish (a flag nothing sets), the
+    waits run out: the update reports RELEARN_ERR_TIMEOUT within seconds, applies
+    nothing, and the context stays usable (its next update equals a fresh one's)."""
+    import time
+    from paper_2509_26193_gb300 import relearn as R
+    net = workloads.gaussian_clusters(n=20000, clusters=4, side=2000, std=150, seed=81,
+                                      sigma=300.0)
+    g = GpuNet(net)
+    R.relearn_debug_stall_reduce(g.ctx, 3)
+    t0 = time.time()
+    with pytest.raises(R.RelearnError) as ei:
+        g.update(step=0)
+    assert ei.value.status == R.ERR_TIMEOUT
+    assert time.time() - t0 < 20
+    ga, gd = g.vacancies()
+    assert np.array_equal(ga, net.vac_ax) and np.array_equal(gd, net.vac_de)
+    assert len(g.synapses()[0]) == 0
+    ref = GpuNet(net)
+    for h in (g, ref):
+        h.update(step=1)
+    for a, b in zip(g.requests(), ref.requests()):
+        assert np.array_equal(a, b)
+    assert np.array_equal(np.stack(g.synapses()), np.stack(ref.synapses()))
+    g.close()
+    ref.close()
+
+
 def test_checkpoint_resume_is_bit_identical():
     from paper_2509_26193_gb300 import relearn as R
     net = workloads.gaussian_clusters(n=20000, clusters=4, side=2000, std=150, seed=90,
