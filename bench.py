@@ -831,7 +831,7 @@ def run_diff(args):
     warm(step, max(args.warmup, 3))
     m = step()
     torch.cuda.synchronize()
-    mean0 = float(m)
+    mean0 = float(m.detach())
     e0 = R.relearn_get_last_stats(ctx)["length_evals_total"]
     l0 = R.relearn_launch_count()
     clocks = ClockSampler(device.index)

@@ -142,7 +142,7 @@ def test_autograd_op_and_sigma_calibration():
     m = mean_synapse_length(ctx, x, y, z, sigma, va, vd, 0.3)
     m.backward()
     ref = _gpu(net, 0.3)
-    assert float(m) == pytest.approx(ref["mean"], rel=1e-12)
+    assert float(m.detach()) == pytest.approx(ref["mean"], rel=1e-12)
     assert float(sigma.grad) == pytest.approx(ref["dsigma"], rel=1e-6)
     assert np.allclose(x.grad.cpu().numpy(), ref["g"][:, 0], rtol=0, atol=1e-9 + 1e-5 *
                        np.abs(ref["g"]).max())
