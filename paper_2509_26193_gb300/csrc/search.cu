@@ -444,8 +444,9 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                         ckk[nck] = comp;
                         ++nck;
                     }
+                    int k = 0;
 #pragma unroll 1
-                    for (int k = 0; k < kCkStride && p < root_end; ++k) {
+                    for (; k < kCkStride && p < root_end; ++k) {
                         const float4 g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[p].g));
                         const int2 t = __ldg(reinterpret_cast<const int2 *>(&a.nodes[p].t));
                         const float d2 = dist2(x, g);
@@ -458,8 +459,8 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                                 kahan_add(cum, comp, attraction(g.w, d2, k2, k2sh));
                         }
                         p = __any_sync(0xffffffffu, on && !pass) ? p + 1 : max(t.x, p + 1);
-                        ++steps;
                     }
+                    steps += k;
                 }
             } else {
                 while (__any_sync(0xffffffffu, p < root_end)) {
