@@ -86,7 +86,7 @@ struct Src {
 __device__ __forceinline__ void fwd_visit(Fwd &f, float cnt, float D, float k2, float k2sh)
 {
     const float at = att(cnt, D, k2, k2sh);
-    const float d = __fsqrt_rn(D);
+    const float d = sqrt_approx(D);
     kahan(f.s, f.sc, at);
     kahan(f.a, f.ac, __fmul_rn(at, d));
     kahan(f.b, f.bc, __fmul_rn(at, D));
@@ -99,10 +99,10 @@ __device__ __forceinline__ void bwd_visit(Bwd &b, const Src &s, float cnt, float
                                           float &oy, float &oz)
 {
     const float q = __fmul_rn(att(cnt, D, k2, s.k2sh), s.invS);
-    const float d = __fsqrt_rn(D);
+    const float d = sqrt_approx(D);
     const float dl = __fsub_rn(d, s.l);
     b.cov = __fmaf_rn(__fmul_rn(q, dl), __fsub_rn(D, s.Db), b.cov);
-    const float inv_d = d > 0.0f ? __frcp_rn(d) : 0.0f;
+    const float inv_d = d > 0.0f ? rcp_approx(d) : 0.0f;
     const float kap = __fmul_rn(__fmul_rn(q, __fmaf_rn(two_s2, dl, -inv_d)), s.w);
     ox = __fmul_rn(kap, rx);
     oy = __fmul_rn(kap, ry);
