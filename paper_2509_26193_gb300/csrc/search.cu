@@ -509,8 +509,10 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
         const int32_t i = a.perm[s];
         const int32_t nq = max(a.vac_ax[i], 0);
         const int32_t qbase = a.qoff_o[i];
-        const double lns0 = S > 0.0 ? log(S) - (double)k2sh * 0.6931471805599453
-                                    : -__longlong_as_double(0x7ff0000000000000LL);
+        // ln S for the diagnostics only (an FP64 log per source otherwise wasted)
+        const double lns0 = !a.diag_lns ? 0.0
+                            : S > 0.0   ? log(S) - (double)k2sh * 0.6931471805599453
+                                        : -__longlong_as_double(0x7ff0000000000000LL);
         for (int32_t e = 0; e < nq; ++e) {
             int32_t result = -1, evals = own, draws = 0;
             if (S > 0.0) {
@@ -823,8 +825,10 @@ __global__ void __launch_bounds__(256) bh_split_kernel(SearchArgs a)
         const int32_t i = a.perm[s];
         const int32_t nq = max(a.vac_ax[i], 0);
         const int32_t qbase = a.qoff_o[i];
-        const double lns0 = S > 0.0 ? log(S) - (double)k2sh * 0.6931471805599453
-                                    : -__longlong_as_double(0x7ff0000000000000LL);
+        // ln S for the diagnostics only (an FP64 log per source otherwise wasted)
+        const double lns0 = !a.diag_lns ? 0.0
+                            : S > 0.0   ? log(S) - (double)k2sh * 0.6931471805599453
+                                        : -__longlong_as_double(0x7ff0000000000000LL);
         for (int32_t e = lane; e < nq; e += 32) {
             int32_t result = -1, evals = own, draws = 0;
             if (S > 0.0) {
