@@ -216,47 +216,55 @@ class Runner:
         self.extra_flags = extra_flags
         self.dev = device
         n = net.n
-        d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
-        self.x, self.y, self.z = d(net.x), d(net.y), d(net.z)
-        self.vac_ax0, self.vac_de0 = d(net.vac_ax), d(net.vac_de)
-        self.vac_ax, self.vac_de = self.vac_ax0.clone(), self.vac_de0.clone()
-        self.type = d(net.type)
         self.spk_host = [workloads.spikes(n, net.seed, u) for u in range(UPDATES_PER_STEP)]
-        self.spiked = [d(s) for s in self.spk_host]
         self.retract_host = np.full(n, 1 << 20, np.int32)
-        self.retract = d(self.retract_host)
+        # a step's inputs live in one device buffer, each array at a 256-byte aligned
+        # offset, so that the end-to-end variant brings them over with one copy from
+        # one pinned host buffer of the same layout
+        arrays = [("x", net.x), ("y", net.y), ("z", net.z), ("vac_ax", net.vac_ax),
+                  ("vac_de", net.vac_de), ("type", net.type), ("retract", self.retract_host)]
+        arrays += [(f"spiked{u}", sp) for u, sp in enumerate(self.spk_host)]
+        layout, off = {}, 0
+        for name, a in arrays:
+            a = np.ascontiguousarray(a)
+            layout[name] = (off, a)
+            off += (a.nbytes + 255) // 256 * 256
+        host = np.zeros(off, np.uint8)
+        for name, (o, a) in layout.items():
+            host[o:o + a.nbytes] = a.view(np.uint8).ravel()
+        self.h_in = torch.from_numpy(host).pin_memory()
+        self.dev_in = self.h_in.to(device)
+        tdt = {np.dtype(np.float32): torch.float32, np.dtype(np.int32): torch.int32,
+               np.dtype(np.uint8): torch.uint8}
+        view = lambda name: self.dev_in[layout[name][0]:layout[name][0] + layout[name][1].nbytes] \
+            .view(tdt[layout[name][1].dtype])
+        self.x, self.y, self.z = view("x"), view("y"), view("z")
+        self.vac_ax0, self.vac_de0 = view("vac_ax"), view("vac_de")
+        self.vac_ax, self.vac_de = self.vac_ax0.clone(), self.vac_de0.clone()
+        self.type = view("type")
+        self.retract = view("retract")
+        self.spiked = [view(f"spiked{u}") for u in range(UPDATES_PER_STEP)]
         self.input = torch.zeros(n, dtype=torch.int32, device=device)
         cap = int(min(net.vac_ax.sum(), net.vac_de.sum())) + 1024
         self.ctx = R.relearn_create(n, cap, 0, device=device.index)
         self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
-        # pinned host copies for the end-to-end variant
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        self.h = {"x": pin(net.x), "y": pin(net.y), "z": pin(net.z), "vac_ax": pin(net.vac_ax),
-                  "vac_de": pin(net.vac_de), "type": pin(net.type),
-                  "spiked": [pin(s) for s in self.spk_host], "retract": pin(self.retract_host)}
         self.h_out = torch.empty(n, dtype=torch.int32).pin_memory()
         self.h_cnt = torch.empty(2, dtype=torch.int64).pin_memory()
         self.step_index = 0
 
     def h2d_bytes(self):
-        n = self.net.n
-        return 12 * n + 8 * n + n + UPDATES_PER_STEP * n + 4 * n
+        return int(self.h_in.numel())  # the one input copy of a step (payload + alignment)
 
     def d2h_bytes(self):
         return 4 * self.net.n + 16
 
     def step(self, e2e=False, timing=True):
         R, torch = self.R, self.torch
-        if e2e:  # this step's inputs arrive from pinned host memory
-            for name, dst in (("x", self.x), ("y", self.y), ("z", self.z),
-                              ("vac_ax", self.vac_ax), ("vac_de", self.vac_de),
-                              ("type", self.type), ("retract", self.retract)):
-                dst.copy_(self.h[name], non_blocking=True)
-            for u in range(UPDATES_PER_STEP):
-                self.spiked[u].copy_(self.h["spiked"][u], non_blocking=True)
-        else:    # element-model output for this step: the initial vacancies
-            self.vac_ax.copy_(self.vac_ax0)
-            self.vac_de.copy_(self.vac_de0)
+        if e2e:  # this step's inputs arrive from pinned host memory, one copy
+            self.dev_in.copy_(self.h_in, non_blocking=True)
+        # element-model output for this step: the initial vacancies
+        self.vac_ax.copy_(self.vac_ax0)
+        self.vac_de.copy_(self.vac_de0)
         R.relearn_build_octree(self.ctx, self.x, self.y, self.z)
         base = 1000 * self.step_index
         for u in range(UPDATES_PER_STEP):
@@ -301,13 +309,8 @@ class Runner:
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(st)
-            if e2e:  # this step's inputs arrive from pinned host memory
-                for name, dst in (("x", self.x), ("y", self.y), ("z", self.z),
-                                  ("vac_ax", self.vac_ax0), ("vac_de", self.vac_de0),
-                                  ("type", self.type), ("retract", self.retract)):
-                    dst.copy_(self.h[name], non_blocking=True)
-                for u in range(UPDATES_PER_STEP):
-                    self.spiked[u].copy_(self.h["spiked"][u], non_blocking=True)
+            if e2e:  # this step's inputs arrive from pinned host memory, one copy
+                self.dev_in.copy_(self.h_in, non_blocking=True)
             self.graph.replay()
             if e2e:
                 self.h_out.copy_(self.input, non_blocking=True)
@@ -474,10 +477,13 @@ def run_ours(args):
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
+        ck2 = ClockSampler(device.index)
+        ck2.start()
         r2 = run.timed_graph(args.steps, e2e=True) if args.graph else run.timed(args.steps, True)
+        clk2 = ck2.stop()
         u2, s2 = aggregate(r2["searches"], r2["ms"] / 1000.0, ws, device)
         e2e = {"value": u2 / s2, "unit": UNIT, "h2d_bytes_per_step": run.h2d_bytes(),
-               "d2h_bytes_per_step": run.d2h_bytes()}
+               "d2h_bytes_per_step": run.d2h_bytes(), "clocks": clk2}
     if ws > 1:
         dist.barrier()
     if rank != 0:
@@ -714,10 +720,13 @@ def run_batch(args):
     units, secs = aggregate(res["searches"], res["ms"] / 1000.0, ws, device)
     e2e = None
     if not args.no_e2e:
+        ck2 = ClockSampler(device.index)
+        ck2.start()
         r2 = run.timed(args.steps, e2e=True)
+        clk2 = ck2.stop()
         u2, s2 = aggregate(r2["searches"], r2["ms"] / 1000.0, ws, device)
         e2e = {"value": u2 / s2, "unit": UNIT, "h2d_bytes_per_step": run.h2d_bytes(),
-               "d2h_bytes_per_step": run.d2h_bytes()}
+               "d2h_bytes_per_step": run.d2h_bytes(), "clocks": clk2}
     if ws > 1:
         dist.barrier()
         if rank != 0:
@@ -843,10 +852,13 @@ def run_diff(args):
     units, secs = aggregate(units_per_step * args.steps, ms / 1000.0, ws, device)
     e2e = None
     if not args.no_e2e:
+        ck2 = ClockSampler(device.index)
+        ck2.start()
         ms2 = timed(args.steps, e2e=True)
+        clk2 = ck2.stop()
         u2, s2 = aggregate(units_per_step * args.steps, ms2 / 1000.0, ws, device)
         e2e = {"value": u2 / s2, "unit": UNIT, "h2d_bytes_per_step": 20 * net.n,
-               "d2h_bytes_per_step": 12 * net.n}
+               "d2h_bytes_per_step": 12 * net.n, "clocks": clk2}
     # sigma calibration: 50 Adam steps toward a 600 um mean length
     torch.cuda.synchronize()
     t0 = time.perf_counter()
