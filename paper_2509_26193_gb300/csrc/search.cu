@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
 // kernel's; only the association of the FP32/FP64 sums differs, so a draw can
 // differ from the union kernel's only within rounding of a cumulative boundary.
 constexpr int kSplitRanges = 512; // ranges per source (the list stops growing there)
-constexpr int kSplitMinRest = 64; // a rest of fewer nodes is not handed out
+constexpr int kSplitMinRest = 32; // a rest of fewer nodes is not handed out
 
 // The source's candidates in [b, e), compensated sum from zero, until the running
 // total exceeds rel: that candidate, else the last with weight, else -1. The same
