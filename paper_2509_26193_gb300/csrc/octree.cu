@@ -376,11 +376,19 @@ __global__ void topo_emit_kernel(const uint32_t *__restrict__ codes,
 
 // The root of network b is the first node at its first Morton position; its
 // escape index is where the next network's tree starts.
+// Network roots; and node m (one past the last node, inside the node array) as a
+// sentinel for walks that step past the end: no count, escape m + 1.
 __global__ void roots_kernel(const int32_t *__restrict__ base, const int64_t *__restrict__ off,
-                             int32_t B, int32_t *__restrict__ root)
+                             int32_t B, int32_t *__restrict__ root, Node *nodes,
+                             const int64_t *d_num_nodes)
 {
     const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < B) root[b] = base[off[b]];
+    if (b == 0) {
+        const int64_t m = *d_num_nodes;
+        nodes[m].g = NodeGeo{0.f, 0.f, 0.f, 0.f};
+        nodes[m].t = NodeTopo{(int32_t)(m + 1), 0u, -1, 0};
+    }
 }
 
 // Bottom-up update as prefix sums (Sec. III-B "Division of work": an inner node
@@ -659,7 +667,8 @@ cudaError_t octree_build(relearn_ctx *c, int64_t n, int32_t B, const float *x, c
     topo_emit_kernel<<<gn, 256, 0, st>>>(c->d_codes, net, c->d_off, n, c->d_mask, c->d_base,
                                          c->d_nodes, c->d_parent, c->d_nsize, c->d_leaf);
     note_launch();
-    roots_kernel<<<gb, 256, 0, st>>>(c->d_base, c->d_off, B, c->d_root);
+    roots_kernel<<<gb, 256, 0, st>>>(c->d_base, c->d_off, B, c->d_root, c->d_nodes,
+                                     c->d_i64 + I64_NODES);
     note_launch();
     return cudaGetLastError();
 }

@@ -240,6 +240,12 @@ __device__ __forceinline__ WalkOut walk(const Node *__restrict__ nodes, int32_t 
     return o;
 }
 
+// One step of a 32-lane union walk at node p (see bh_search_kernel).
+__device__ __forceinline__ void union_step(const Node *__restrict__ nodes, int32_t &p,
+                                           int32_t &skip, float &cum, float &comp,
+                                           int32_t &own, float3 x, int32_t self_node,
+                                           uint32_t thr0, float k2, float k2sh);
+
 // Kahan step: sum + a with the rounding error carried in c (explicit round-to-
 // nearest operations, so every pass reproduces the same bits).
 __device__ __forceinline__ void kahan_add(float &sum, float &c, float a)
@@ -248,6 +254,24 @@ __device__ __forceinline__ void kahan_add(float &sum, float &c, float a)
     const float t = __fadd_rn(sum, y);
     c = __fsub_rn(__fsub_rn(t, sum), y);
     sum = t;
+}
+
+__device__ __forceinline__ void union_step(const Node *__restrict__ nodes, int32_t &p,
+                                           int32_t &skip, float &cum, float &comp,
+                                           int32_t &own, float3 x, int32_t self_node,
+                                           uint32_t thr0, float k2, float k2sh)
+{
+    const float4 g = __ldg(reinterpret_cast<const float4 *>(&nodes[p].g));
+    const int2 t = __ldg(reinterpret_cast<const int2 *>(&nodes[p].t));
+    const float d2 = dist2(x, g);
+    const bool on = p >= skip && g.w > 0.0f;
+    const bool pass = __float_as_uint(d2) + (uint32_t)t.y > thr0;
+    own += on ? 1 : 0;
+    if (on && pass) {
+        skip = t.x;
+        if (p != self_node) kahan_add(cum, comp, attraction(g.w, d2, k2, k2sh));
+    }
+    p = __any_sync(0xffffffffu, on && !pass) ? p + 1 : max(t.x, p + 1);
 }
 
 // Draw on the root frontier from a checkpoint: the lane's own walk with pass 1's
@@ -445,23 +469,25 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                         ++nck;
                     }
                     int k = 0;
+                    if constexpr (!kBatched) {
+                        // two steps per test: node root_end is a sentinel (no count,
+                        // escape root_end + 1), so a step past the end changes nothing
 #pragma unroll 1
-                    for (; k < kCkStride && p < root_end; ++k) {
-                        const float4 g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[p].g));
-                        const int2 t = __ldg(reinterpret_cast<const int2 *>(&a.nodes[p].t));
-                        const float d2 = dist2(x, g);
-                        const bool on = p >= skip && g.w > 0.0f;
-                        const bool pass = __float_as_uint(d2) + (uint32_t)t.y > thr0;
-                        own += on ? 1 : 0;
-                        if (on && pass) {
-                            skip = t.x;
-                            if (p != self_node)
-                                kahan_add(cum, comp, attraction(g.w, d2, k2, k2sh));
+                        for (; k < kCkStride && p < root_end; k += 2) {
+                            union_step(a.nodes, p, skip, cum, comp, own, x, self_node, thr0, k2,
+                                       k2sh);
+                            union_step(a.nodes, p, skip, cum, comp, own, x, self_node, thr0, k2,
+                                       k2sh);
                         }
-                        p = __any_sync(0xffffffffu, on && !pass) ? p + 1 : max(t.x, p + 1);
+                    } else {
+#pragma unroll 1
+                        for (; k < kCkStride && p < root_end; ++k)
+                            union_step(a.nodes, p, skip, cum, comp, own, x, self_node, thr0, k2,
+                                       k2sh);
                     }
                     steps += k;
                 }
+                if (p > root_end) --steps; // the sentinel's step
             } else {
                 while (__any_sync(0xffffffffu, p < root_end)) {
                     const bool run = p < root_end; // uniform within the group
