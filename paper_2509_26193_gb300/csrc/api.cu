@@ -217,7 +217,7 @@ relearn_status relearn_create_batched(relearn_ctx **out, int device, int64_t max
     A(d_posq, N);
     A(d_mask, N);
     A(d_base, N + 1);
-    A(d_nodes, M);
+    A(d_nodes, M + 4); // + sentinels past the last node
     A(d_parent, M);
     A(d_nsize, M);
     A(d_leaf, N);

@@ -376,16 +376,16 @@ __global__ void topo_emit_kernel(const uint32_t *__restrict__ codes,
 
 // The root of network b is the first node at its first Morton position; its
 // escape index is where the next network's tree starts.
-// Network roots; and node m (one past the last node, inside the node array) as a
-// sentinel for walks that step past the end: no count, escape m + 1.
+// Network roots; and nodes m .. m + 2 (past the last node, inside the node array)
+// as sentinels for walks that step past the end: no count, escape = next node.
 __global__ void roots_kernel(const int32_t *__restrict__ base, const int64_t *__restrict__ off,
                              int32_t B, int32_t *__restrict__ root, Node *nodes,
                              const int64_t *d_num_nodes)
 {
     const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < B) root[b] = base[off[b]];
-    if (b == 0) {
-        const int64_t m = *d_num_nodes;
+    if (b < 3) {
+        const int64_t m = *d_num_nodes + b;
         nodes[m].g = NodeGeo{0.f, 0.f, 0.f, 0.f};
         nodes[m].t = NodeTopo{(int32_t)(m + 1), 0u, -1, 0};
     }

@@ -470,14 +470,15 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                     }
                     int k = 0;
                     if constexpr (!kBatched) {
-                        // two steps per test: node root_end is a sentinel (no count,
-                        // escape root_end + 1), so a step past the end changes nothing
+                        // four steps per test: nodes root_end .. root_end + 2 are
+                        // sentinels (no count, escape = next node), so steps past the
+                        // end change nothing
 #pragma unroll 1
-                        for (; k < kCkStride && p < root_end; k += 2) {
-                            union_step(a.nodes, p, skip, cum, comp, own, x, self_node, thr0, k2,
-                                       k2sh);
-                            union_step(a.nodes, p, skip, cum, comp, own, x, self_node, thr0, k2,
-                                       k2sh);
+                        for (; k < kCkStride && p < root_end; k += 4) {
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+                                union_step(a.nodes, p, skip, cum, comp, own, x, self_node, thr0,
+                                           k2, k2sh);
                         }
                     } else {
 #pragma unroll 1
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                     }
                     steps += k;
                 }
-                if (p > root_end) --steps; // the sentinel's step
+                if (p > root_end) steps -= p - root_end; // the sentinels' steps
             } else {
                 while (__any_sync(0xffffffffu, p < root_end)) {
                     const bool run = p < root_end; // uniform within the group
