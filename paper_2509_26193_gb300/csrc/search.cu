@@ -8,14 +8,18 @@
 // searches then draws from it (results are exactly those of separate searches).
 //
 // Root pass (pass 1): the 32 lanes of a warp take 32 neurons that are adjacent
-// in Morton order and walk the UNION of their frontiers together. Nodes are in
-// pre-order with skip links, so the walk is stackless: the warp descends
-// (p + 1) if any lane rejects the node under the acceptance criterion, else
-// jumps to the node's escape index. A lane that accepted a node ignores the
-// node's subtree; every node is loaded once per warp (one broadcast load), and
-// each lane still meets exactly its own candidates in Morton order, which is the
-// order of the cumulative draw. Every kCkStride warp steps each lane stores a
-// checkpoint (its next own node, its running sum).
+// in Morton order and walk the UNION of their frontiers together (or, when they
+// straddle a cell boundary, one union per piece). Nodes are in pre-order with
+// skip links, so the walk is stackless: the warp descends (p + 1) if any lane
+// rejects the node under the acceptance criterion, else jumps to the node's
+// escape index. A lane that accepted a node ignores the node's subtree; every
+// node is loaded once per union (one broadcast load), and each lane still meets
+// exactly its own candidates in Morton order, which is the order of the
+// cumulative draw. Every kCkStride union steps each lane stores a checkpoint
+// (its next own node, its running sum).
+//
+// Updates with few sources run bh_split_kernel instead (one warp per source, its
+// frontier walk shared out among the lanes; see there).
 //
 // Sums: each lane accumulates its own terms in FP32 with Kahan compensation (the
 // running total is sum - c, accurate to a few ulp whatever the number of terms);
