@@ -351,13 +351,18 @@ class Runner:
 def first_update_profile(runner):
     """Phase times of the first (largest) update of a step, for the breakdown."""
     R = runner.R
+    torch = runner.torch
     runner.vac_ax.copy_(runner.vac_ax0)
     runner.vac_de.copy_(runner.vac_de0)
-    R.relearn_build_octree(runner.ctx, runner.x, runner.y, runner.z)
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record()
+    R.relearn_build_octree(runner.ctx, runner.x, runner.y, runner.z)  # a1-a3
+    b1.record()
     p = R.params(runner.net.sigma, runner.theta, runner.net.seed, 0, runner.extra_flags,
                  runner.group)
     s = R.relearn_update_connectivity(runner.ctx, p, runner.vac_ax, runner.vac_de, runner.type,
                                       stats=True)
+    s["ms_build"] = b0.elapsed_time(b1)
     p = R.params(runner.net.sigma, runner.theta, runner.net.seed, 999)
     R.relearn_delete_synapses(runner.ctx, p, runner.retract, runner.retract, runner.vac_ax,
                               runner.vac_de)
@@ -505,6 +510,15 @@ def run_ours(args):
                     f"{res['kernel_launches']} launches",
             "kernel_ms_per_launch": res["kernel_ms"] / max(res["kernel_launches"], 1),
             "kernel_share_of_step": res["kernel_ms"] / res["ms"]}
+    # the second ALU ceiling: one ex2 on the special-function unit per node evaluation
+    # at most, 16 per SM per clock
+    mufu_peak = SM_COUNT * 16 * clock_mhz * 1e6 / 1e12
+    mufu = res["evals"] / (res["kernel_ms"] / 1000.0) / 1e12 if res["kernel_ms"] > 0 else 0.0
+    roof["secondary"] = {"mufu": {"achieved": mufu, "peak": mufu_peak, "unit": "T ex2/s",
+                                  "frac": mufu / mufu_peak,
+                                  "peak_source": f"derived: {SM_COUNT} SMs x 16 ex2 per clock x "
+                                                 f"{clock_mhz:.0f} MHz",
+                                  "work": "at most one ex2 per node evaluation"}}
     line = {"metric": METRIC, "value": units / secs, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": res["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -517,6 +531,7 @@ def run_ours(args):
                                  "ms_search": prof["ms_search"],
                                  "ms_search_kernel": prof["ms_search_kernel"],
                                  "ms_accept": prof["ms_accept"], "ms_apply": prof["ms_apply"],
+                                 "ms_build_a1_a3": prof["ms_build"],
                                  "searches_per_s": prof["searches"] / (prof["ms_total"] / 1e3)},
                 "evals_per_search": res["evals"] / max(res["searches"], 1),
                 "search_group": args.group or "default",
