@@ -45,6 +45,7 @@ struct SearchConst {
 struct relearn_ctx {
     int device = 0;
     int num_sms = 0;
+    int search_occ[2][2] = {{0, 0}, {0, 0}}; // resident blocks per SM: [batched][union, split]
     int64_t max_neurons = 0, max_synapses = 0, max_searches = 0, max_nodes = 0;
     int32_t max_nets = 1; // networks one build may hold
     int32_t num_nets = 1; // networks in the current tree

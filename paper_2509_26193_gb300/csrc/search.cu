@@ -1025,16 +1025,21 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     a.spread_depth = depths ? (int)((sg - 1000) / 100) : kSpreadDepth;
     void (*kern)(SearchArgs) = a.net ? bh_search_kernel<true> : bh_search_kernel<false>;
     void (*split)(SearchArgs) = a.net ? bh_split_kernel<true> : bh_split_kernel<false>;
-    int per_sm = 0, per_sm_split = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0))) return e;
-    if ((e = cudaFuncSetAttribute(split, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kSplitSmem)))
-        return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_split, split, 256,
-                                                           kSplitSmem)))
-        return e;
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm_split < 1) per_sm_split = 1;
+    // resident blocks per SM of both kernels, queried once per context and kernel pair
+    int *occ = c->search_occ[a.net ? 1 : 0];
+    if (occ[0] == 0) {
+        int per_sm = 0, per_sm_split = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0))) return e;
+        if ((e = cudaFuncSetAttribute(split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kSplitSmem)))
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_split, split, 256,
+                                                               kSplitSmem)))
+            return e;
+        occ[0] = per_sm < 1 ? 1 : per_sm;
+        occ[1] = per_sm_split < 1 ? 1 : per_sm_split;
+    }
+    const int per_sm = occ[0], per_sm_split = occ[1];
     // the union kernel serves 32 sources per warp; with few sources per resident warp
     // it would leave the GPU mostly idle (kernel choice and widths: see kSplitWaves)
     const int64_t warps = (int64_t)c->num_sms * per_sm * 8;
