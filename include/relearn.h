@@ -69,8 +69,8 @@ typedef struct relearn_ctx relearn_ctx;
  *             2 = one source per warp, its frontier walk shared out over the 32 lanes;
  *             0 = the default: one source per warp when the update has at most 9 sources
  *             per resident warp of the union kernel, else unions chosen per warp: its 32
- *             sources (Morton order) cut at the boundaries of depth-4 cells, one union
- *             per piece;
+ *             sources (Morton order) cut at the boundaries of cells of depth 2 when at
+ *             least 30 % of the neurons search, else of depth 4, one union per piece;
  *             1000 + 100 * d + r (d = 0..10, r = 0..10, r unused) = the default with the
  *             pieces cut at the boundaries of depth-d cells;
  *             3000 + f (f = 0..999) = the default with one source per warp for updates of

@@ -46,10 +46,14 @@ constexpr int kCkStride = 128; // warp steps between checkpoints
 constexpr int kMaxCk = 128;    // checkpoints kept per lane (later steps reuse the last one)
 constexpr float kTiny = 8.673617e-19f; // 2^-60
 // Walks per warp (see bh_search_kernel): the warp's 32 sources are cut into pieces
-// at the boundaries of cells of depth kSpreadDepth, and each piece walks one union
-// (update 0 of the 2^20-neuron clustered network: 73 % of warps form one piece; the
-// others used to walk lane by lane or in unions of 8).
-constexpr int kSpreadDepth = 4;
+// at the boundaries of cells of some depth, and each piece walks one union. When
+// most neurons are sources (at least kDenseTenths / 10 of them), consecutive sources
+// are close and unions across a cell boundary stay compact: cut only at depth
+// kCutDense. Sparse sources spread further: cut at depth kCutSparse. Per-update
+// sweeps (2^20-neuron clustered network, first three updates, 86 / 40 / 15 % of the
+// neurons searching): depth 2 8.18 / 4.29 / 2.83 ms, depth 4 8.44 / 4.28 / 2.37 ms;
+// a batch of 256 uniform networks, 86 % searching: depth 2 234.9 ms, depth 4 274.2 ms.
+constexpr int kCutDense = 2, kCutSparse = 4, kDenseTenths = 3;
 // The default also looks at how many sources the update has, per resident warp of
 // the union kernel (W = 7,296 on 152 SMs). Per-update sweeps on the 2^20-neuron
 // clustered network (ten successive updates, 907k down to 2.4k sources): with at
@@ -167,7 +171,8 @@ struct SearchArgs {
     uint64_t seed;
     uint32_t step;
     int forced_group; // 0 = choose per warp; 1, 8, 16, 32 = union width; 2 = split
-    int spread_depth;  // a union of 32 needs all sources in one cell this deep
+    int spread_depth;  // cut depth of union pieces (-1: the default by source density)
+    int64_t n_total;   // neurons of all networks
     int32_t split_below; // with forced_group 0: split kernel for at most this many sources
     // deferred restarts (RELEARN_FLAG_REGROUP): searches whose first draw is an inner
     // node are queued here and finished after a sort by that node (subtree order)
@@ -427,7 +432,10 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
             uint32_t code = live ? a.codes[s] : 0u;
             code = __shfl_sync(0xffffffffu, code, live ? lane : last);
             const uint32_t nxt = __shfl_down_sync(0xffffffffu, code, 1);
-            bool cut = lane < 31 && morton_common_digits(code, nxt) < a.spread_depth;
+            const int depth = a.spread_depth >= 0                          ? a.spread_depth
+                              : (int64_t)A * 10 >= kDenseTenths * a.n_total ? kCutDense
+                                                                            : kCutSparse;
+            bool cut = lane < 31 && morton_common_digits(code, nxt) < depth;
             if constexpr (kBatched) {
                 const int32_t nn = __shfl_down_sync(0xffffffffu, net, 1);
                 cut = cut || (lane < 31 && nn != net);
@@ -1022,7 +1030,8 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     const uint32_t sg = p.search_group;
     a.forced_group = sg < 1000 ? (int)sg : 0;
     const bool depths = sg >= 1000 && sg < 3000;
-    a.spread_depth = depths ? (int)((sg - 1000) / 100) : kSpreadDepth;
+    a.spread_depth = depths ? (int)((sg - 1000) / 100) : -1;
+    a.n_total = c->n;
     void (*kern)(SearchArgs) = a.net ? bh_search_kernel<true> : bh_search_kernel<false>;
     void (*split)(SearchArgs) = a.net ? bh_split_kernel<true> : bh_split_kernel<false>;
     // resident blocks per SM of both kernels, queried once per context and kernel pair
