@@ -327,6 +327,30 @@ def test_edge_cases():
     g.close()
 
 
+@pytest.mark.parametrize("group", [32, 1, 2])
+def test_tiny_networks_every_kernel(group):
+    """Networks of 1 to 40 neurons through each search path (unions of 32, lanes alone,
+    one warp per source): the union walk steps past the last node onto the sentinel
+    nodes there, which must change nothing. Requests against the oracle's."""
+    from paper_2509_26193_gb300 import relearn as R
+    for n in (1, 2, 3, 5, 9, 33, 40):
+        net = workloads.uniform_cube(n=n, seed=90 + n)
+        net.vac_ax[:] = 2
+        net.vac_de[:] = 3
+        g = GpuNet(net)
+        p = R.params(net.sigma, net.theta, net.seed, 4, R.FLAG_DIAG, group)
+        st = R.relearn_update_connectivity(g.ctx, p, g.vac_ax, g.vac_de, g.type, stats=True)
+        gt, _ = g.requests()
+        t = oracle.Tree(net.x, net.y, net.z)
+        t.reduce(net.vac_de)
+        qi, qe, (ot, od) = _oracle_searches(net, t, 4, net.theta)
+        assert st["searches"] == len(qi) == 2 * n
+        bad, exempt, exempt_diff = compare_targets(gt, ot, od)
+        assert bad == 0, (n, group, bad)
+        assert st["failed"] == int((gt < 0).sum())
+        g.close()
+
+
 def test_capacity_overflow_is_reported_and_nothing_applied():
     from paper_2509_26193_gb300 import relearn as R
     net = workloads.uniform_cube(n=2000, seed=80)
