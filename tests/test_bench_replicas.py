@@ -49,3 +49,34 @@ def test_aggregate_two_ranks_gloo():
 def test_single_rank_passthrough():
     import bench
     assert bench.aggregate(123.0, 0.25, 1) == (123.0, 0.25)
+
+
+def test_search_traffic_is_tied_to_the_kernel_sources(monkeypatch):
+    """roofline.traffic comes from the committed ncu summary only while the search
+    sources hash to the value recorded there; any other sources give None."""
+    import builtins
+    import hashlib
+    import io
+
+    import bench
+    assert isinstance(bench.search_traffic(), (int, type(None)))
+    files = {f: f"// {f}\n".encode() for f in ("search.cu", "device.cuh", "octree.cu")}
+    h = hashlib.sha256()
+    for f in ("search.cu", "device.cuh", "octree.cu"):
+        h.update(files[f])
+    summary = f"x\nsources-sha256: {h.hexdigest()}\ntraffic-bytes-per-launch: 1234\n"
+    real_open = builtins.open
+
+    def fake_open(path, mode="r", *args, **kwargs):
+        name = os.path.basename(str(path))
+        if name in files:
+            return io.BytesIO(files[name])
+        if name == "bh_search_traffic_gaussian_clusters_2p20.md":
+            return io.StringIO(summary)
+        return real_open(path, mode, *args, **kwargs)
+
+    monkeypatch.setattr(builtins, "open", fake_open)
+    monkeypatch.setattr(bench.os.path, "exists", lambda path: True)
+    assert bench.search_traffic() == 1234
+    files["search.cu"] = b"// changed\n"
+    assert bench.search_traffic() is None
