@@ -41,6 +41,18 @@ def test_host_argument_errors_need_no_gpu(L):
                                   None) == relearn.ERR_INVALID_ARG
     assert L.relearn_philox4x32_10(None, None, None, -1, None) == relearn.ERR_INVALID_ARG
     assert L.relearn_philox4x32_10(None, None, None, 0, None) == relearn.OK
+    # the batched, typed, differentiable and rate entry points, the testing hook
+    assert L.relearn_create_batched(None, 0, 10, 10, 0, 2) == relearn.ERR_INVALID_ARG
+    assert L.relearn_build_octree_batch(None, 2, None, None, None, None, None,
+                                        None) == relearn.ERR_INVALID_ARG
+    assert L.relearn_update_connectivity_typed(None, ctypes.byref(p), None, None, None, None,
+                                               None, None) == relearn.ERR_INVALID_ARG
+    assert L.relearn_mean_length(None, ctypes.byref(p), None, None, None, None,
+                                 None) == relearn.ERR_INVALID_ARG
+    assert L.relearn_mean_length_backward(None, None, None, None, None, None, None, None,
+                                          None) == relearn.ERR_INVALID_ARG
+    assert L.relearn_deliver_rates(None, None, 1, 0, None, None) == relearn.ERR_INVALID_ARG
+    assert L.relearn_debug_stall_reduce(None, 0) == relearn.ERR_INVALID_ARG
     msg = ctypes.c_char_p()
     assert L.relearn_last_error(None, ctypes.byref(msg)) == relearn.ERR_INVALID_ARG
     assert L.relearn_destroy(None) == relearn.OK
