@@ -193,3 +193,58 @@ def test_far_source_does_not_underflow(orc):
     a = np.array([0.0, 1.0, math.exp(-100.0 / 1e4)])
     assert np.allclose(p[:3], a / a.sum(), rtol=1e-9)
     assert t.search(100.0, 0.3, 3, 0, 0, 0)["target"] in (1, 2)
+
+
+@pytest.mark.parametrize("long_axis", [0, 1, 2])
+def test_cell_length_is_longest_edge(orc, long_axis):
+    """Reading R2 (Sec. II criterion, Sec. III-B cells): in an anisotropic box the cell
+    "length" is the longest edge of the cell. Box 4 x 16 x 4 (long axis rotated through
+    x, y, z). A source with no vacancies and one near neuron sit in the first depth-1
+    cell (2 x 8 x 2); a three-neuron cluster sits alone in a second one, each member
+    alone in its own depth-2 cell. The cluster cell's centroid is at distance d from
+    the source; theta is chosen so that theta * d falls between two edge readings:
+      theta = 0.4:  theta d = 5.20: longest edge 8 rejects (members drawn one by one);
+                    the short edges (2), the cube root of the volume (3.17) accept;
+      theta = 0.63: theta d = 8.20: longest edge 8 accepts (one candidate, then a
+                    restart inside the cluster); the cell diagonal (8.49) rejects.
+    Closed-form marginals, written out per case."""
+    def put(p):   # (short, long, short) -> long axis at long_axis
+        p = np.asarray(p, np.float64)
+        out = np.empty_like(p)
+        short = [a for a in range(3) if a != long_axis]
+        out[:, long_axis] = p[:, 1]
+        out[:, short[0]] = p[:, 0]
+        out[:, short[1]] = p[:, 2]
+        return out
+    base = np.array([[0.5, 0.5, 0.5],     # source (no vacant dendritic elements)
+                     [0.5, 1.5, 0.5],     # near neuron
+                     [0.5, 14.5, 0.5],    # cluster member c1
+                     [1.5, 14.5, 0.5],    # c2
+                     [0.5, 10.5, 0.5]])   # c3
+    pts = put(base).astype(np.float32)
+    lo = np.zeros(3, np.float32)
+    hi = put([[4.0, 16.0, 4.0]])[0].astype(np.float32)
+    vac = np.array([0, 1, 1, 2, 1], np.int32)
+    t = orc.Tree(pts[:, 0], pts[:, 1], pts[:, 2], lo, hi)
+    t.reduce(vac)
+    sigma = 10.0
+    s2 = sigma ** 2
+    x0 = base[0]
+    d2 = ((base - x0) ** 2).sum(1)             # 0, 1, 196, 197, 100
+    w = vac[2:].astype(np.float64)
+    cen = (w[:, None] * base[2:]).sum(0) / w.sum()   # (1.0, 13.5, 0.5)
+    dc = math.sqrt(((cen - x0) ** 2).sum())    # 13.0096...
+    assert 8.0 < 0.63 * dc < math.sqrt(2 * 2 + 8 * 8 + 2 * 2)
+    assert (2 * 8 * 2) ** (1 / 3) < 0.4 * dc < 8.0
+    a_near = math.exp(-d2[1] / s2)
+    a_mem = w * np.exp(-d2[2:] / s2)
+    # theta = 0.4: every member is a candidate of the root frontier
+    want = np.array([0.0, a_near, *a_mem]) / (a_near + a_mem.sum())
+    got = t.marginals(sigma, 0.4, 0)
+    assert np.allclose(got[:5], want, rtol=1e-12, atol=1e-15)
+    # theta = 0.63: the cluster cell is one candidate (count 4 at its centroid)
+    a_cl = w.sum() * math.exp(-dc ** 2 / s2)
+    p_cl = a_cl / (a_near + a_cl)
+    want = np.array([0.0, 1 - p_cl, *(p_cl * a_mem / a_mem.sum())])
+    got = t.marginals(sigma, 0.63, 0)
+    assert np.allclose(got[:5], want, rtol=1e-12, atol=1e-15)
