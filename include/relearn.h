@@ -349,6 +349,22 @@ relearn_status relearn_collect_search_times(relearn_ctx *ctx, double *total_ms, 
  * `count` is a host pointer. Never fails for a non-NULL pointer. */
 relearn_status relearn_launch_count(int64_t *count);
 
+/* Measurement probes for the roofline denominators (no counterpart in the paper; used by
+ * the benchmark to measure, on the GPU at hand, the rates that bound the search):
+ *   kind 1  FP32 FMA issue (independent chains of fma.rn.f32), *ops = FMAs;
+ *   kind 2  special-function unit ex2.approx.ftz.f32, *ops = ex2 evaluations;
+ *   kind 3  L2 read bandwidth: `iters` passes of 16-byte L2-only loads over buf,
+ *           *ops = bytes read (buf 16-byte aligned, buf_len >= 4 floats);
+ *   kind 4  packed FP32 FMA (fma.rn.f32x2), *ops = FMAs (two per instruction).
+ * One launch of about 4 blocks of 256 threads per SM on `stream`; the caller times it.
+ * buf is a caller-owned device float[buf_len]; kinds 1, 2 and 4 overwrite up to one
+ * element per thread, kind 3 only reads it. `ops` is a host pointer written before the
+ * launch. Errors: INVALID_ARG for iters < 1, a NULL pointer, an unknown kind or a bad
+ * kind-3 buffer (nothing launched); CUDA when a launch error is already pending (left
+ * pending) or the launch fails. */
+relearn_status relearn_peak_probe(int32_t kind, int64_t iters, float *buf, int64_t buf_len,
+                                  int64_t *ops, void *stream);
+
 /* Allocation-free Morton ordering, for callers that must not allocate device memory
  * (no counterpart in the paper; it exists for users of this library): the neurons'
  * 30-bit Morton codes (same quantisation as relearn_build_octree) and their stable
@@ -360,10 +376,14 @@ relearn_status relearn_launch_count(int64_t *count);
  *   perm         device int32[n], out: perm[k] = id of the neuron with the k-th code
  *                (ties by id), the same order relearn_get_tree reports.
  * The sort's scratch is one static device array of about 8.5 MB per GPU, held until the
- * process exits. The first call on each device looks up that array's device address
- * (with the device current); make that first call before any stream capture. All calls
- * on a device share the array: calls whose GPU work overlaps race and give wrong
- * results, so order them on one stream (or otherwise). Asynchronous on `stream`. */
+ * process exits. Every call looks up that array's device address on the current device
+ * (a lookup, no allocation); the first call on each device also reads its SM count and
+ * may make the driver load this library's kernels there, so make that first call before
+ * any stream capture. All calls on a device share the array: calls whose GPU work
+ * overlaps race and give wrong results, so order them on one stream (or otherwise).
+ * A launch error left pending by earlier, unrelated work makes the call return
+ * RELEARN_ERR_CUDA at once, launching nothing and leaving that error pending for its
+ * owner. Asynchronous on `stream`. */
 #define RELEARN_NOALLOC_MAX_NEURONS (1 << 20)
 relearn_status relearn_morton_order_noalloc(int64_t n, const float *x, const float *y,
                                             const float *z, const float *box_lo3,

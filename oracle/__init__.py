@@ -93,7 +93,8 @@ def lib():
                 "orc_delete": (_I64, [_I64, _P, _P, _P, _P, _U64, _U64, _P, _P, _P, _P]),
                 "orc_deliver_spikes": (None, [_I64, _I64, _P, _P, _P, _P, _P]),
                 "orc_deliver_rates": (None, [_I64, _I64, _P, _P, _P, _P, _U64, _U64, _P]),
-                "orc_mean_length": (_D, [_P, _D, _D, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
+                "orc_mean_length": (_D, [_P, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                         _P, ctypes.c_int]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -363,19 +364,25 @@ def mean_length(tree: Tree, sigma, theta, vac_ax, vac_de, grad=True, threads=1):
     """Differentiable form: L = sum_i m_i l_i / sum_i m_i, l_i the attraction-weighted
     mean distance from source i to the centroids of its root frontier (m = vac_ax).
     The tree must have been reduced with the same vac_de. Returns a dict with
-    mean, ell (per neuron, NaN when excluded) and, with grad, dsigma and the position
-    gradient g (n x 3)."""
+    mean, ell (per neuron, NaN when excluded), margin_ac (per neuron: the smallest
+    relative distance of a root-frontier criterion test from its tie, inf when none)
+    and, with grad, dsigma, the position gradient g (n x 3) and g_abs (n x 3), the same
+    sums over the magnitudes of their terms (the scale of their rounding error)."""
     va = _c(vac_ax, np.int32)
     vd = _c(vac_de, np.int32)
     n = tree.n
     ell = np.zeros(n, np.float64)
     ds = np.zeros(1, np.float64)
     g = [np.zeros(n, np.float64) for _ in range(3)] if grad else [None] * 3
+    ga = [np.zeros(n, np.float64) for _ in range(3)] if grad else [None] * 3
+    margin = np.zeros(n, np.float64)
     m = lib().orc_mean_length(tree._h, float(sigma), float(theta), _p(va), _p(vd), _p(ell),
-                              _p(ds), *(_p(a) for a in g), int(threads))
-    out = {"mean": float(m), "ell": ell, "dsigma": float(ds[0])}
+                              _p(ds), *(_p(a) for a in g), _p(margin), *(_p(a) for a in ga),
+                              int(threads))
+    out = {"mean": float(m), "ell": ell, "dsigma": float(ds[0]), "margin_ac": margin}
     if grad:
         out["g"] = np.stack(g, 1)
+        out["g_abs"] = np.stack(ga, 1)
     return out
 
 

@@ -983,10 +983,16 @@ void orc_deliver_rates(int64_t n, int64_t nsyn, const int32_t *s_src, const int3
  *                 bottom-up centroid is the w-weighted mean).
  * ell (per neuron, NAN for excluded sources), dsigma and the position
  * gradients gx, gy, gz are optional outputs; returns L (NAN when M = 0).
+ * margin (optional, per neuron) is a diagnostic for the comparison with FP32:
+ * min |len^2 - theta^2 d^2| / len^2 over the criterion tests of the source's
+ * root frontier (INFINITY when there are none or the neuron is no source).
+ * ax, ay, az (optional, with the gradients) are the same sums as gx, gy, gz taken
+ * over the magnitudes of their terms: the scale against which the rounding error of
+ * a sum of terms of both signs is measured (|g| <= a, equal without cancellation).
  * Optional OpenMP over the independent sources (threads). */
 /* ------------------------------------------------------------------------- */
 static int root_frontier(const OTree *T, int32_t i, double sigma, double theta, Frontier *F,
-                         double *a, double *S_out)
+                         double *a, double *S_out, double *margin_out)
 {
     double x[3] = {T->px[i], T->py[i], T->pz[i]};
     SearchCtx s;
@@ -997,11 +1003,13 @@ static int root_frontier(const OTree *T, int32_t i, double sigma, double theta, 
     s.self = i;
     s.margin_ac = INFINITY;
     F->n = 0;
+    if (margin_out) *margin_out = INFINITY;
     if (T->n_nodes == 0 || T->nodes[0].leaf) {
         *S_out = 0.0;
         return 0;
     }
     expand(T, 0, &s, F);
+    if (margin_out) *margin_out = s.margin_ac;
     double dmin2 = INFINITY; /* common factor exp(dmin2 / sigma^2): q is unchanged */
     for (int64_t k = 0; k < F->n; ++k)
         if (!F->e[k].self && F->e[k].d2 < dmin2) dmin2 = F->e[k].d2;
@@ -1016,7 +1024,8 @@ static int root_frontier(const OTree *T, int32_t i, double sigma, double theta, 
 
 double orc_mean_length(void *t, double sigma, double theta, const int32_t *vac_ax,
                        const int32_t *vac_de, double *ell, double *dsigma, double *gx,
-                       double *gy, double *gz, int threads)
+                       double *gy, double *gz, double *margin, double *ax, double *ay,
+                       double *az, int threads)
 {
     const OTree *T = (const OTree *)t;
     const int64_t n = T->n;
@@ -1035,9 +1044,10 @@ double orc_mean_length(void *t, double sigma, double theta, const int32_t *vac_a
 #endif
         for (int64_t i = 0; i < n; ++i) {
             lsrc[i] = NAN;
+            if (margin) margin[i] = INFINITY;
             if (vac_ax[i] <= 0) continue;
             double S;
-            root_frontier(T, (int32_t)i, sigma, theta, &F, a, &S);
+            root_frontier(T, (int32_t)i, sigma, theta, &F, a, &S, margin ? &margin[i] : NULL);
             if (!(S > 0.0)) continue;
             double l = 0.0, Db = 0.0;
             for (int64_t k = 0; k < F.n; ++k) {
@@ -1061,7 +1071,13 @@ double orc_mean_length(void *t, double sigma, double theta, const int32_t *vac_a
     if (gx && gy && gz) {
         /* pass 2: dL/dc_k accumulated per node (G), direct terms per source */
         double *G = (double *)calloc((size_t)(T->n_nodes ? T->n_nodes : 1) * 3, sizeof(double));
+        const int mag = ax && ay && az;
+        double *Ga = mag ? (double *)calloc((size_t)(T->n_nodes ? T->n_nodes : 1) * 3,
+                                            sizeof(double))
+                         : NULL;
         for (int64_t j = 0; j < n; ++j) gx[j] = gy[j] = gz[j] = 0.0;
+        if (mag)
+            for (int64_t j = 0; j < n; ++j) ax[j] = ay[j] = az[j] = 0.0;
 #ifdef _OPENMP
 #pragma omp parallel num_threads(threads)
 #endif
@@ -1074,7 +1090,7 @@ double orc_mean_length(void *t, double sigma, double theta, const int32_t *vac_a
             for (int64_t i = 0; i < n; ++i) {
                 if (!(M > 0) || !(lsrc[i] == lsrc[i])) continue; /* excluded source */
                 double S;
-                root_frontier(T, (int32_t)i, sigma, theta, &F, a, &S);
+                root_frontier(T, (int32_t)i, sigma, theta, &F, a, &S, NULL);
                 const double w = vac_ax[i] / M, l = lsrc[i];
                 for (int64_t k = 0; k < F.n; ++k) {
                     if (F.e[k].self || a[k] == 0.0) continue;
@@ -1090,6 +1106,13 @@ double orc_mean_length(void *t, double sigma, double theta, const int32_t *vac_a
 #endif
                         G[3 * F.e[k].node + c] += g;
                         (c == 0 ? gx : c == 1 ? gy : gz)[i] -= g;
+                        if (mag) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                            Ga[3 * F.e[k].node + c] += fabs(g);
+                            (c == 0 ? ax : c == 1 ? ay : az)[i] += fabs(g);
+                        }
                     }
                 }
             }
@@ -1101,17 +1124,26 @@ double orc_mean_length(void *t, double sigma, double theta, const int32_t *vac_a
             const ONode *nv = &T->nodes[v];
             if (!nv->leaf) continue;
             int j = nv->neuron;
-            double h[3] = {0, 0, 0};
+            double h[3] = {0, 0, 0}, ha[3] = {0, 0, 0};
             for (int64_t u = v; u >= 0; u = T->nodes[u].parent) {
                 const ONode *nu = &T->nodes[u];
                 if (nu->count > 0)
-                    for (int c = 0; c < 3; ++c) h[c] += G[3 * u + c] / nu->count;
+                    for (int c = 0; c < 3; ++c) {
+                        h[c] += G[3 * u + c] / nu->count;
+                        if (mag) ha[c] += Ga[3 * u + c] / nu->count;
+                    }
             }
             gx[j] += vac_de[j] * h[0];
             gy[j] += vac_de[j] * h[1];
             gz[j] += vac_de[j] * h[2];
+            if (mag) {
+                ax[j] += vac_de[j] * ha[0];
+                ay[j] += vac_de[j] * ha[1];
+                az[j] += vac_de[j] * ha[2];
+            }
         }
         free(G);
+        free(Ga);
     }
     free(lsrc);
     return M > 0 ? sum / M : NAN;

@@ -17,13 +17,20 @@
 // FP32 attractions with Kahan-compensated sums; S, l and Dbar formed in FP64 and
 // kept per source with the exponent shift. Backward: the same walk again,
 // recomputing every attraction (nothing per candidate is stored), accumulating
-// the centroid adjoints G_k = sum_i (m_i / M) dl_i/dc_k per node (one 16-byte
-// vector atomic add per lane and candidate: all lanes of a union walk add to the
-// same node in one instruction, which the memory system combines; measured 1.65x
-// faster than a warp shuffle reduction followed by FP64 atomics, with a gradient
-// norm error of 1.6e-5 instead of 3e-6 against the FP64 oracle at 2^18 neurons)
-// and each source's direct term in registers; then every neuron j adds
-// w_j * sum over its cells k of G_k / N_k (its leaf's parent chain, in FP64).
+// the centroid adjoints G_k = sum_i (m_i / M) dl_i/dc_k per node in FP64 and each
+// source's direct term in registers (Kahan-compensated FP32: it is a sum of terms of
+// both signs that nearly cancel); then every neuron j adds w_j * sum over its cells
+// k of G_k / N_k (its leaf's parent chain, in FP64).
+//
+// Node adjoints: in a union walk every lane that takes a candidate takes the same
+// node at the same step, so the warp first sums its lanes' (x, y, z) contributions
+// (a transpose reduction: five shuffle levels that leave each component's total on
+// eight lanes) and three lanes add the totals to the node with FP64 atomics; a warp
+// cut into pieces does this once per piece that took a candidate. One FP32 vector
+// atomic per lane and candidate (the previous design) was L2-atomic-bound and its
+// order-dependent FP32 sums left element-wise gradient errors up to 6e-3 of the
+// cancellation-aware scale at 2^18 neurons; FP64 sums of warp partials bring every
+// element within the FP32 arithmetic of its terms.
 #include "internal.h"
 
 namespace rl {
@@ -48,7 +55,7 @@ struct LenArgs {
     double *lsum;   // [4]
     int32_t *work;
     // backward
-    float4 *G;           // [nodes] centroid adjoints (x, y, z, unused)
+    double *G;           // [4 * nodes] centroid adjoints (x, y, z, unused) in FP64
     float *gx, *gy, *gz; // id order
     const double *gout;  // upstream gradient of the mean (NULL = 1)
     double *gsigma;
@@ -74,6 +81,7 @@ struct Fwd {
 
 struct Bwd {
     float cov = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+    float cx = 0.f, cy = 0.f, cz = 0.f; // Kahan compensation of the direct term
 };
 
 struct Src {
@@ -107,14 +115,47 @@ __device__ __forceinline__ void bwd_visit(Bwd &b, const Src &s, float cnt, float
     ox = __fmul_rn(kap, rx);
     oy = __fmul_rn(kap, ry);
     oz = __fmul_rn(kap, rz);
-    b.gx = __fsub_rn(b.gx, ox);
-    b.gy = __fsub_rn(b.gy, oy);
-    b.gz = __fsub_rn(b.gz, oz);
+    kahan(b.gx, b.cx, -ox);
+    kahan(b.gy, b.cy, -oy);
+    kahan(b.gz, b.cz, -oz);
 }
 
-__device__ __forceinline__ void add_node(float4 *G, int32_t p, float ox, float oy, float oz)
+// One lane's own contribution straight to the node (lane-by-lane walks, rare).
+__device__ __forceinline__ void add_node(double *G, int32_t p, float ox, float oy, float oz)
 {
-    atomicAdd(&G[p], make_float4(ox, oy, oz, 0.0f));
+    atomicAdd(&G[4 * (int64_t)p + 0], (double)ox);
+    atomicAdd(&G[4 * (int64_t)p + 1], (double)oy);
+    atomicAdd(&G[4 * (int64_t)p + 2], (double)oz);
+}
+
+// Sum of (x, y, z) over the 32 lanes (every lane calls it). Transpose reduction: at
+// offset 16 a lane keeps two of the four values (x, y, z, 0) and sends the other
+// two; at offset 8 it keeps one; offsets 4, 2, 1 sum that one. Afterwards lanes
+// 0-7 hold the total of x, 8-15 of y, 16-23 of z. Returns this lane's total.
+__device__ __forceinline__ float warp_sum3(float x, float y, float z, int lane)
+{
+    const bool hi = lane & 16;
+    float k0 = hi ? z : x, k1 = hi ? 0.0f : y;
+    const float s0 = hi ? x : z, s1 = hi ? y : 0.0f;
+    k0 = __fadd_rn(k0, __shfl_xor_sync(0xffffffffu, s0, 16));
+    k1 = __fadd_rn(k1, __shfl_xor_sync(0xffffffffu, s1, 16));
+    const bool b3 = lane & 8;
+    float k = b3 ? k1 : k0;
+    k = __fadd_rn(k, __shfl_xor_sync(0xffffffffu, b3 ? k0 : k1, 8));
+    k = __fadd_rn(k, __shfl_xor_sync(0xffffffffu, k, 4));
+    k = __fadd_rn(k, __shfl_xor_sync(0xffffffffu, k, 2));
+    k = __fadd_rn(k, __shfl_xor_sync(0xffffffffu, k, 1));
+    return k;
+}
+
+// The warp's contributions to node p (every lane calls it with the same p; lanes
+// that took no candidate pass zeros): summed across the warp, then added to the
+// node's FP64 adjoint by lanes 0, 8 and 16 (x, y, z).
+__device__ __forceinline__ void add_node_warp(double *G, int32_t p, float ox, float oy, float oz,
+                                              int lane)
+{
+    const float t = warp_sum3(ox, oy, oz, lane);
+    if ((lane & 7) == 0 && lane < 24) atomicAdd(&G[4 * (int64_t)p + (lane >> 3)], (double)t);
 }
 
 // A lane's own walk of its root frontier (stackless: expand = p + 1, accept or
@@ -147,8 +188,12 @@ __device__ int32_t lane_walk(const LenArgs &a, const Src &s, int32_t end, uint32
     return visited;
 }
 
+#ifndef RELEARN_LEN_BWD_MIN_BLOCKS
+#define RELEARN_LEN_BWD_MIN_BLOCKS 5 // the adjoint's warp sums need more than 40 registers
+#endif
 template <bool kBack>
-__global__ void __launch_bounds__(256, 6) length_kernel(LenArgs a)
+__global__ void __launch_bounds__(256, kBack ? RELEARN_LEN_BWD_MIN_BLOCKS : 6)
+    length_kernel(LenArgs a)
 {
     const int32_t A = (int32_t)*a.d_total;
     const int lane = threadIdx.x & 31;
@@ -228,10 +273,17 @@ __global__ void __launch_bounds__(256, 6) length_kernel(LenArgs a)
                 if constexpr (!kBack) {
                     if (take) fwd_visit(f, g.w, D, k2, 0.0f);
                 } else {
-                    if (take) {
-                        float ox, oy, oz;
-                        bwd_visit(b, s, g.w, rx, ry, rz, D, k2, two_s2, ox, oy, oz);
-                        add_node(a.G, p, ox, oy, oz);
+                    float ox = 0.0f, oy = 0.0f, oz = 0.0f;
+                    if (take) bwd_visit(b, s, g.w, rx, ry, rz, D, k2, two_s2, ox, oy, oz);
+                    // one warp sum per piece that took a candidate at this step
+                    const uint32_t took = __ballot_sync(0xffffffffu, take) & gmask;
+                    uint32_t heads = __ballot_sync(0xffffffffu, lane == first && took != 0u);
+                    while (heads) {
+                        const int h = __ffs(heads) - 1;
+                        heads &= heads - 1;
+                        const bool mine = first == h;
+                        add_node_warp(a.G, __shfl_sync(0xffffffffu, p, h), mine ? ox : 0.0f,
+                                      mine ? oy : 0.0f, mine ? oz : 0.0f, lane);
                     }
                 }
                 const uint32_t down = __ballot_sync(0xffffffffu, on && !pass) & gmask;
@@ -253,11 +305,9 @@ __global__ void __launch_bounds__(256, 6) length_kernel(LenArgs a)
                 if constexpr (!kBack) {
                     if (take) fwd_visit(f, g.w, D, k2, 0.0f);
                 } else {
-                    if (take) {
-                        float ox, oy, oz;
-                        bwd_visit(b, s, g.w, rx, ry, rz, D, k2, two_s2, ox, oy, oz);
-                        add_node(a.G, p, ox, oy, oz);
-                    }
+                    float ox = 0.0f, oy = 0.0f, oz = 0.0f;
+                    if (take) bwd_visit(b, s, g.w, rx, ry, rz, D, k2, two_s2, ox, oy, oz);
+                    if (__any_sync(0xffffffffu, take)) add_node_warp(a.G, p, ox, oy, oz, lane);
                 }
                 p = __any_sync(0xffffffffu, on && !pass) ? p + 1 : max(t.x, p + 1);
             }
@@ -287,9 +337,9 @@ __global__ void __launch_bounds__(256, 6) length_kernel(LenArgs a)
             a.state[sp] = st;
         } else {
             if (!on_src) continue;
-            a.gx[i] = b.gx;
-            a.gy[i] = b.gy;
-            a.gz[i] = b.gz;
+            a.gx[i] = __fsub_rn(b.gx, b.cx);
+            a.gy[i] = __fsub_rn(b.gy, b.cy);
+            a.gz[i] = __fsub_rn(b.gz, b.cz);
             my0 += (double)s.w * (double)b.cov; // * 2 / sigma^3 below
         }
     }
@@ -352,12 +402,12 @@ __global__ void len_finish_kernel(const float4 *__restrict__ state,
     }
 }
 
-__global__ void zero_nodes_kernel(float4 *G, const int64_t *d_num_nodes)
+__global__ void zero_nodes_kernel(double4 *G, const int64_t *d_num_nodes)
 {
     const int64_t m = *d_num_nodes;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
          k += (int64_t)gridDim.x * blockDim.x)
-        G[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        G[k] = make_double4(0.0, 0.0, 0.0, 0.0);
 }
 
 // Neuron j (Morton position s) gets w_j * sum over its cells k of G_k / N_k.
@@ -365,7 +415,7 @@ __global__ void len_scatter_kernel(const Node *__restrict__ nodes,
                                    const int32_t *__restrict__ parent,
                                    const int32_t *__restrict__ leaf_of,
                                    const int32_t *__restrict__ perm,
-                                   const int32_t *__restrict__ vac_de, const float4 *__restrict__ G,
+                                   const int32_t *__restrict__ vac_de, const double *__restrict__ G,
                                    int64_t n, float *gx, float *gy, float *gz)
 {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
@@ -378,14 +428,14 @@ __global__ void len_scatter_kernel(const Node *__restrict__ nodes,
             const int32_t cnt = nodes[u].t.icount;
             if (cnt <= 0) continue;
             const double inv = 1.0 / (double)cnt;
-            const float4 gu = G[u];
-            hx += (double)gu.x * inv;
-            hy += (double)gu.y * inv;
-            hz += (double)gu.z * inv;
+            hx += G[4 * (int64_t)u + 0] * inv;
+            hy += G[4 * (int64_t)u + 1] * inv;
+            hz += G[4 * (int64_t)u + 2] * inv;
         }
-        gx[i] += (float)(w * hx);
-        gy[i] += (float)(w * hy);
-        gz[i] += (float)(w * hz);
+        // direct term (FP32) + cell terms (FP64), rounded once
+        gx[i] = (float)((double)gx[i] + w * hx);
+        gy[i] = (float)((double)gy[i] + w * hy);
+        gz[i] = (float)((double)gz[i] + w * hz);
     }
 }
 
@@ -454,10 +504,10 @@ cudaError_t length_backward(relearn_ctx *c, const int32_t *vac_ax, const int32_t
 {
     cudaError_t e;
     const int64_t n = c->n;
-    // d_acc is free between bottom-up updates (32 bytes per node; 16 used here)
-    float4 *G = reinterpret_cast<float4 *>(c->d_acc);
+    // d_acc is free between bottom-up updates (32 bytes per node: x, y, z in FP64)
+    double *G = c->d_acc;
     zero_nodes_kernel<<<grid_for(c->max_nodes, 256, c->num_sms), 256, 0, st>>>(
-        G, c->d_i64 + I64_NODES);
+        reinterpret_cast<double4 *>(G), c->d_i64 + I64_NODES);
     note_launch();
     for (float *g : {gx, gy, gz})
         if ((e = cudaMemsetAsync(g, 0, n * sizeof(float), st))) return e;

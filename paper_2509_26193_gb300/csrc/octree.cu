@@ -726,6 +726,11 @@ constexpr size_t kOffPermAlt = kOffCodesAlt + 4 * size_t(kNoAllocMaxN);
 constexpr size_t kOffHist = kOffPermAlt + 4 * size_t(kNoAllocMaxN);
 constexpr size_t kOffScan = kOffHist + 4 * 256 * size_t(kNoAllocSortBlocks);
 constexpr size_t kNoAllocBytes = kOffScan + 8 * size_t(kNoAllocScanBlocks + 1);
+// the regions must not overlap: the box words (6 x uint32) below the geometry, the
+// geometry below the sort's ping-pong buffers; 8-byte sums on 8-byte boundaries
+static_assert(6 * sizeof(uint32_t) <= kOffGeom, "box words overlap the geometry");
+static_assert(kOffGeom + sizeof(Geom) <= kOffCodesAlt, "geometry overlaps the sort buffers");
+static_assert(kOffHist % 8 == 0 && kOffScan % 8 == 0, "scan sums must be 8-byte aligned");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -734,25 +739,26 @@ struct NoAllocDevice {
     int num_sms = 0;
 };
 std::mutex g_noalloc_mu;
-NoAllocDevice g_noalloc_dev[64];
+int g_noalloc_sms[64]; // SM count per device ordinal, read once
 
-// Once per device, with that device current: look up the array's device address.
+// With the device current: the array's device address (looked up on every call, so
+// that a context re-created after cudaDeviceReset is served with its own address)
+// and the SM count (read once per device).
 relearn_status noalloc_setup(int dev, NoAllocDevice *out)
 {
     if (dev < 0 || dev >= 64) return RELEARN_ERR_INVALID_ARG;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
+        return RELEARN_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    NoAllocDevice &d = g_noalloc_dev[dev];
-    if (!d.base) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
-            return RELEARN_ERR_CUDA;
+    if (g_noalloc_sms[dev] == 0) {
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return RELEARN_ERR_CUDA;
-        d.num_sms = sms > 0 ? sms : 1;
-        d.base = static_cast<unsigned char *>(p);
+        g_noalloc_sms[dev] = sms > 0 ? sms : 1;
     }
-    *out = d;
+    out->base = static_cast<unsigned char *>(p);
+    out->num_sms = g_noalloc_sms[dev];
     return RELEARN_OK;
 }
 
@@ -775,6 +781,9 @@ extern "C" relearn_status relearn_morton_order_noalloc(int64_t n, const float *x
     if (sort_blocks_needed(n) > kNoAllocSortBlocks ||
         scan_blocks_needed(256 * sort_blocks_needed(n)) > kNoAllocScanBlocks)
         return RELEARN_ERR_CAPACITY;
+    // a launch error left pending by earlier work belongs to its owner: refuse the call
+    // and leave it pending, so that the checks below see this call's launches only
+    if (cudaPeekAtLastError() != cudaSuccess) return RELEARN_ERR_CUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RELEARN_ERR_CUDA;
     NoAllocDevice d;
@@ -807,6 +816,7 @@ extern "C" relearn_status relearn_morton_order_noalloc(int64_t n, const float *x
     note_launch();
     morton_kernel<<<grid, 256, 0, st>>>(x, y, z, n, nullptr, 1, geom, codes, nullptr, perm);
     note_launch();
+    if (cudaGetLastError() != cudaSuccess) return RELEARN_ERR_CUDA;
     int which = 0;
     if (radix_sort_u32(codes, codes_alt, perm, perm_alt, n, nullptr, 30, ss, st, &which) !=
         cudaSuccess)

@@ -87,6 +87,7 @@ _SIGS = {
     "relearn_collect_search_times": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)],
     "relearn_launch_count": [ctypes.POINTER(_I64)],
     "relearn_morton_order_noalloc": [_I64, _P, _P, _P, _P, _P, _P, _P, _P],
+    "relearn_peak_probe": [ctypes.c_int32, _I64, _P, _I64, ctypes.POINTER(_I64), _P],
     "relearn_last_error": [_P, ctypes.POINTER(ctypes.c_char_p)],
 }
 
@@ -219,6 +220,19 @@ def relearn_destroy(ctx):
     ctx.close()
 
 
+def _box_corners(box_lo, box_hi):
+    """Host float32[3] copies of a caller-given domain box (both corners or none)."""
+    if (box_lo is None) != (box_hi is None):
+        raise ValueError("give both box corners or none")
+    if box_lo is None:
+        return None, None
+    lo = np.ascontiguousarray(box_lo, np.float32).ravel()
+    hi = np.ascontiguousarray(box_hi, np.float32).ravel()
+    if lo.size != 3 or hi.size != 3:
+        raise ValueError("each box corner holds 3 floats (x, y, z)")
+    return lo, hi
+
+
 def relearn_build_octree(ctx, x, y, z, vac_de=None, box_lo=None, box_hi=None, stream=None):
     torch = _torch()
     n = x.numel()
@@ -226,12 +240,7 @@ def relearn_build_octree(ctx, x, y, z, vac_de=None, box_lo=None, box_hi=None, st
     py = _dev_ptr(y, torch.float32, n, "y")
     pz = _dev_ptr(z, torch.float32, n, "z")
     pv = None if vac_de is None else _dev_ptr(vac_de, torch.int32, n, "vac_de")
-    lo = hi = None
-    if (box_lo is None) != (box_hi is None):
-        raise ValueError("give both box corners or none")
-    if box_lo is not None:
-        lo = np.ascontiguousarray(box_lo, np.float32)
-        hi = np.ascontiguousarray(box_hi, np.float32)
+    lo, hi = _box_corners(box_lo, box_hi)
     st = lib().relearn_build_octree(ctx.handle, n, px, py, pz, pv, _np_ptr(lo), _np_ptr(hi),
                                     _stream(stream))
     _raise(ctx, st, "relearn_build_octree")
@@ -463,13 +472,25 @@ def relearn_morton_order_noalloc(x, y, z, codes, perm, box_lo=None, box_hi=None,
     pz = _dev_ptr(z, torch.float32, n, "z")
     pc = _dev_ptr(codes, torch.int32, n, "codes")
     pp = _dev_ptr(perm, torch.int32, n, "perm")
-    lo = hi = None
-    if box_lo is not None:
-        lo = np.ascontiguousarray(box_lo, np.float32)
-        hi = np.ascontiguousarray(box_hi, np.float32)
+    lo, hi = _box_corners(box_lo, box_hi)
     st = lib().relearn_morton_order_noalloc(n, px, py, pz, _np_ptr(lo), _np_ptr(hi), pc, pp,
                                             _stream(stream))
     _raise(None, st, "relearn_morton_order_noalloc")
+
+
+PROBE_FMA, PROBE_EX2, PROBE_L2, PROBE_FMA2 = 1, 2, 3, 4
+
+
+def relearn_peak_probe(kind, iters, buf, stream=None):
+    """Launches one measurement probe on the current stream (see relearn.h); returns the
+    work of the launch (FMAs, ex2 evaluations or bytes read). The caller times it."""
+    torch = _torch()
+    pb = _dev_ptr(buf, torch.float32, buf.numel(), "buf")
+    ops = ctypes.c_int64()
+    st = lib().relearn_peak_probe(int(kind), int(iters), pb, buf.numel(), ctypes.byref(ops),
+                                  _stream(stream))
+    _raise(None, st, "relearn_peak_probe")
+    return int(ops.value)
 
 
 def relearn_last_error(ctx):

@@ -51,20 +51,22 @@ def test_single_rank_passthrough():
     assert bench.aggregate(123.0, 0.25, 1) == (123.0, 0.25)
 
 
-def test_search_traffic_is_tied_to_the_kernel_sources(monkeypatch):
-    """roofline.traffic comes from the committed ncu summary only while the search
-    sources hash to the value recorded there; any other sources give None."""
+def test_profile_counters_are_tied_to_the_kernel_sources(monkeypatch):
+    """roofline.traffic (and the issue-active share) come from the committed ncu
+    summary only while the search sources hash to the value recorded there; any
+    other sources give no counters."""
     import builtins
     import hashlib
     import io
 
     import bench
-    assert isinstance(bench.search_traffic(), (int, type(None)))
+    assert isinstance(bench.profile_counters(), dict)
     files = {f: f"// {f}\n".encode() for f in ("search.cu", "device.cuh", "octree.cu")}
     h = hashlib.sha256()
     for f in ("search.cu", "device.cuh", "octree.cu"):
         h.update(files[f])
-    summary = f"x\nsources-sha256: {h.hexdigest()}\ntraffic-bytes-per-launch: 1234\n"
+    summary = (f"x\nsources-sha256: {h.hexdigest()}\ntraffic-bytes-per-launch: 1234\n"
+               f"issue-active-first-update: 71.5\n")
     real_open = builtins.open
 
     def fake_open(path, mode="r", *args, **kwargs):
@@ -77,6 +79,6 @@ def test_search_traffic_is_tied_to_the_kernel_sources(monkeypatch):
 
     monkeypatch.setattr(builtins, "open", fake_open)
     monkeypatch.setattr(bench.os.path, "exists", lambda path: True)
-    assert bench.search_traffic() == 1234
+    assert bench.profile_counters() == {"traffic": 1234.0, "issue_active": 71.5}
     files["search.cu"] = b"// changed\n"
-    assert bench.search_traffic() is None
+    assert bench.profile_counters() == {}

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import AC_MARGIN, LNS_TOL, compare_targets, dev
+from gpu_common import AC_MARGIN, LNS_TOL, check_targets, dev
 from paper_2509_26193_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -64,9 +64,7 @@ def test_batch_search_matches_oracle(theta):
     gt, gacc = R.relearn_get_requests(g.ctx)
     r, va, vd, syn = _oracle(b, 4)
     assert stats["searches"] == len(r["tgt"]) == len(gt)
-    bad, exempt, exempt_diff = compare_targets(gt, r["tgt"], r["diag"])
-    assert bad == 0, (bad, exempt, exempt_diff)
-    assert exempt_diff <= max(2, exempt // 10)
+    exempt_diff = check_targets(gt, r["tgt"], r["diag"], f"batch theta {theta}")["exempt_diff"]
     dg = R.relearn_get_search_diag(g.ctx)
     od = r["diag"]
     fin = np.isfinite(od["ln_s0"])
@@ -292,8 +290,7 @@ def test_full_size_batch_sampled():
             ot, od = t.search_batch(float(b.sigma[k]), b.theta, b.seed, 1, qi_all[sel] - lo,
                                     qe_all[sel], threads=8)
             ot = np.where(ot >= 0, ot + lo, -1)
-            bad, exempt, exempt_diff = compare_targets(gt[sel], ot, od)
-            assert bad == 0, (k, group, bad, exempt, exempt_diff)
+            check_targets(gt[sel], ot, od, f"batch network {k} group {group}")
             # ln S where no criterion test is within FP32 rounding of its tie (there the
             # two frontiers can legitimately differ by a node)
             fin = np.isfinite(od["ln_s0"]) & (od["margin_ac"] >= AC_MARGIN)

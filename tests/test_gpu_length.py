@@ -1,17 +1,29 @@
 """Differentiable form on the GPU (relearn_mean_length / _backward and the torch
 autograd op) against the FP64 oracle.
 
-Tolerances (derived from the arithmetic): every attraction, distance and
-product is one or two FP32 roundings (relative 2^-24 each; ex2.approx adds
-2^-22); the sums are Kahan-compensated and the ratios formed in FP64, so a
-source's length l_i carries a relative error of a few 1e-7 -> l_i and the mean
-within 1e-5 (the stated floating-point bar). The adjoint is a sum of terms of
-both signs whose total is far smaller than its terms (the direct term of a
-source in a uniform cloud nearly cancels), so it is compared in norm:
-|g_gpu - g_oracle|_2 <= 1e-4 |g_oracle|_2 and dL/dsigma within 1e-4 relative.
-At theta > 0 a criterion test within FP32 rounding of its tie can flip a node
-in or out of a frontier on one side only; then a few sources differ and the
-bounds are 1e-3 (norm) and a 0.5 % share of sources beyond 1e-5.
+Tolerances (derived from the arithmetic): every attraction, distance and product
+is one or two FP32 roundings (relative 2^-24 each; the special-function unit adds
+a few 2^-24); the forward sums are Kahan-compensated and the ratios formed in FP64,
+so a source's length l_i, the mean and dL/dsigma carry relative errors of a few
+1e-7: all within 1e-5 (the stated floating-point bar).
+
+The position gradient is a sum of terms of both signs. It is compared element by
+element in two ways:
+  |g_gpu - g_orc| <= 1e-5 |g_orc| + 1e-5 max|g_orc| / sqrt(n)       (a)
+  |g_gpu - g_orc| <= 1e-5 a_orc                                       (b)
+where a_orc is the oracle's sum of the magnitudes of the same terms (the scale of
+the rounding error of any evaluation of the sum). (a) holds at 2^12 and 2^14; its
+floor shrinks like 1/sqrt(n) while FP32 term errors do not, so at 2^18 the bound
+is (b), the componentwise relative error of a sum.
+
+At theta > 0 a criterion test within FP32 rounding of its tie can put a node in or
+out of a source's frontier on one side only. The forward exempts exactly the
+sources with a root-frontier criterion test within 1e-5 of its tie (the oracle
+reports the margin per source). A flip changes that source's contributions to
+every node of its frontier, so the gradient of many neurons, and the gradient
+checks at theta > 0 therefore run on the same network with those sources'
+searches removed (vac_ax = 0 for every source with a margin below 1e-4, on both
+sides), which leaves a tree and frontiers that FP32 reproduces.
 """
 import numpy as np
 import pytest
@@ -56,32 +68,54 @@ def _orc(net, theta, sigma=None, grad=True):
     t = oracle.Tree(net.x, net.y, net.z)
     t.reduce(net.vac_de)
     r = oracle.mean_length(t, net.sigma if sigma is None else sigma, theta, net.vac_ax,
-                           net.vac_de, grad=grad, threads=8)
+                           net.vac_de, grad=grad, threads=16)
     t.close()
     return r
 
 
-def _compare(g, o, theta):
-    exact = theta == 0.0
-    assert abs(g["mean"] - o["mean"]) <= (1e-5 if exact else 1e-5) * o["mean"]
+def _compare_forward(g, o, theta):
+    assert abs(g["mean"] - o["mean"]) <= 1e-5 * o["mean"]
     ok = np.isfinite(o["ell"])
     assert np.array_equal(np.isfinite(g["ell"]), ok)
     rel = np.abs(g["ell"][ok] - o["ell"][ok]) / o["ell"][ok]
-    if exact:
-        assert rel.max() <= 1e-5, rel.max()
-    else:
-        assert np.mean(rel > 1e-5) <= 0.005, np.mean(rel > 1e-5)
-    if "g" in g:
-        nrm = np.linalg.norm(o["g"])
-        err = np.linalg.norm(g["g"] - o["g"]) / nrm
-        assert err <= (1e-4 if exact else 1e-3), err
-        assert abs(g["dsigma"] - o["dsigma"]) <= (1e-4 if exact else 1e-3) * abs(o["dsigma"])
+    near = o["margin_ac"][ok] < 1e-5   # a criterion test within 1e-5 of its tie
+    if theta == 0.0:
+        assert not near.any()
+    assert rel[~near].max() <= 1e-5, rel[~near].max()
+    print(f"forward: max rel {rel[~near].max():.2e}, {int(near.sum())} of {int(ok.sum())} "
+          f"sources exempt (criterion margin < 1e-5)")
 
 
+def _compare_gradient(g, o, n, floor_rule=True):
+    assert abs(g["dsigma"] - o["dsigma"]) <= 1e-5 * abs(o["dsigma"])
+    err = np.abs(g["g"] - o["g"])
+    ra = err / (np.abs(o["g"]) + np.abs(o["g"]).max() / np.sqrt(n))
+    rb = err / np.maximum(o["g_abs"], 1e-300)
+    print(f"gradient n={n}: (a) max {ra.max():.2e}, (b) max {rb.max():.2e}, "
+          f"norm {np.linalg.norm(err) / np.linalg.norm(o['g']):.2e}")
+    assert rb.max() <= 1e-5, rb.max()
+    if floor_rule:
+        assert ra.max() <= 1e-5, ra.max()
+
+
+def _tie_free(net, theta, cut=1e-4):
+    """The same network without the searches of sources whose root frontier has a
+    criterion test within `cut` of its tie (their vac_ax set to 0)."""
+    o = _orc(net, theta, grad=False)
+    near = o["margin_ac"] < cut
+    net.vac_ax = np.where(near, 0, net.vac_ax).astype(np.int32)
+    return net, int(near.sum())
+
+
+@pytest.mark.parametrize("n", [1 << 12, 1 << 14])
 @pytest.mark.parametrize("theta", [0.0, 0.3])
-def test_forward_and_adjoint_match_oracle_2p12(theta):
-    net = workloads.differentiable_cube(n=1 << 12)
-    _compare(_gpu(net, theta), _orc(net, theta), theta)
+def test_forward_and_adjoint_match_oracle(theta, n):
+    net = workloads.differentiable_cube(n=n)
+    _compare_forward(_gpu(net, theta, grad=False), _orc(net, theta, grad=False), theta)
+    if theta > 0:
+        net, removed = _tie_free(net, theta)
+        print(f"{removed} sources near a criterion tie removed for the gradient check")
+    _compare_gradient(_gpu(net, theta), _orc(net, theta), n, floor_rule=n <= 1 << 12)
 
 
 def test_sigma_gradient_matches_fp64_central_difference():
@@ -97,7 +131,10 @@ def test_sigma_gradient_matches_fp64_central_difference():
 
 def test_full_size_2p18():
     net = workloads.differentiable_cube()
-    _compare(_gpu(net, 0.3), _orc(net, 0.3), 0.3)
+    _compare_forward(_gpu(net, 0.3, grad=False), _orc(net, 0.3, grad=False), 0.3)
+    net, removed = _tie_free(net, 0.3)
+    print(f"{removed} sources near a criterion tie removed for the gradient check")
+    _compare_gradient(_gpu(net, 0.3), _orc(net, 0.3), net.n, floor_rule=False)
 
 
 def test_edge_cases():

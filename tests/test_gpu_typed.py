@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import GpuNet, compare_targets, dev
+from gpu_common import GpuNet, check_targets, dev
 from paper_2509_26193_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -91,8 +91,7 @@ def test_typed_matches_oracle_replay():
         qi, qe = oracle.queries(part)
         ot, od = t.search_batch(net.sigma, net.theta, net.seed, step, qi, qe, threads=8)
         assert len(gt) == len(qi) > 0
-        bad, exempt, exempt_diff = compare_targets(gt, ot, od)
-        assert bad == 0, (kind, bad, exempt, exempt_diff)
+        check_targets(gt, ot, od, f"typed pool {kind}")
         assert np.all(pool[gt[gt >= 0]] > 0)
         # acceptance and apply replayed on the GPU's requests
         oacc = oracle.accept(net.n, qi, qe, gt, pool, net.seed, step)

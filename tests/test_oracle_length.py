@@ -58,19 +58,23 @@ def _brute_force(net, sigma):
     kap = Q * (2.0 * (d - ell[:, None]) / sigma ** 2 - inv) * (m / M)[:, None]
     Gij = kap[:, :, None] * R                           # d(m_i l_i / M) / d c_j
     g = -Gij.sum(1) + Gij.sum(0)                        # source term + target (leaf) term
-    return mean, np.where(src, ell, np.nan), dsig, g
+    g_abs = np.abs(Gij).sum(1) + np.abs(Gij).sum(0)     # the same over the terms' magnitudes
+    return mean, np.where(src, ell, np.nan), dsig, g, g_abs
 
 
 def test_theta_zero_is_the_closed_form(orc):
     net = _net(n=1024)
     r = _oracle(orc, net, 0.0)
-    mean, ell, dsig, g = _brute_force(net, net.sigma)
+    mean, ell, dsig, g, g_abs = _brute_force(net, net.sigma)
     assert abs(r["mean"] - mean) <= 1e-12 * mean
     ok = np.isfinite(ell)
     assert np.array_equal(np.isfinite(r["ell"]), ok)
     assert np.allclose(r["ell"][ok], ell[ok], rtol=1e-11, atol=0)
     assert abs(r["dsigma"] - dsig) <= 1e-9 * abs(dsig)
     assert np.allclose(r["g"], g, rtol=1e-8, atol=1e-12 * np.abs(g).max())
+    # the magnitude sums (the rounding-error scale of each gradient element)
+    assert np.allclose(r["g_abs"], g_abs, rtol=1e-10, atol=0)
+    assert np.all(r["g_abs"] >= np.abs(r["g"]) * (1 - 1e-12))
 
 
 def test_two_neurons():
@@ -88,6 +92,7 @@ def test_two_neurons():
     u = np.array([-300.0, -400.0, 0.0]) / 500.0      # unit vector from B to A
     assert np.allclose(r["g"][0], u, atol=1e-12)
     assert np.allclose(r["g"][1], -u, atol=1e-12)
+    assert np.allclose(r["g_abs"], np.abs(r["g"]), atol=1e-12)   # one term each: no cancellation
 
 
 @pytest.mark.parametrize("theta", [0.3, 0.0])
