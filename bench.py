@@ -82,6 +82,9 @@ def parse():
     ap.add_argument("--networks", type=int, default=256)
     ap.add_argument("--main-only", action="store_true",
                     help="skip the theta sweep, the slab and the batched/differentiable forms")
+    ap.add_argument("--launch-list", action="store_true",
+                    help="run two direct steps of the workload (the first a warm-up) and exit: "
+                         "the command profilers capture (prints the launches of one step)")
     return ap.parse_args()
 
 
@@ -415,6 +418,30 @@ class Runner:
         self.torch.cuda.synchronize()
         return {"searches": q1 - q0, "evals_alg": evals, "evals_dedup": e1 - e0}
 
+    def build_graph_ms(self, reps=20):
+        """The octree build (a1-a3) alone, captured in a CUDA graph and replayed: its
+        device time without the host's launch gaps."""
+        torch, R = self.torch, self.R
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            R.relearn_build_octree(self.ctx, self.x, self.y, self.z)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            R.relearn_build_octree(self.ctx, self.x, self.y, self.z)
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
     def close(self):
         self.ctx.close()
 
@@ -617,6 +644,7 @@ def measure_clusters(net, theta, device, args, pk, counters, regroup=False, e2e=
     warm(run.step, max(args.warmup, 3))
     torch.cuda.synchronize()
     dg = run.diag_step()
+    build_ms = run.build_graph_ms() if profile else None
     if args.graph:
         # search-kernel times (library events) come from direct steps; the step time
         # from graph replays of the same step
@@ -630,7 +658,8 @@ def measure_clusters(net, theta, device, args, pk, counters, regroup=False, e2e=
     clk = clocks.stop()
     if args.graph:
         res.update({k: res_k[k] for k in ("kernel_ms", "kernel_launches", "launches")})
-    out = {"res": res, "clocks": clk, "diag": dg, "prof": prof, "runner": run}
+    out = {"res": res, "clocks": clk, "diag": dg, "prof": prof, "runner": run,
+           "build_graph_ms": build_ms}
     if e2e and not args.no_e2e:
         if not args.graph:
             run.step(e2e=True)
@@ -702,6 +731,7 @@ def run_ours(args):
                          "ms_search_kernel": prof["ms_search_kernel"],
                          "ms_accept": prof["ms_accept"], "ms_apply": prof["ms_apply"],
                          "ms_build_a1_a3": prof["ms_build"],
+                         "ms_build_a1_a3_graph": m["build_graph_ms"],
                          "searches_per_s": prof["searches"] / (prof["ms_total"] / 1e3)},
         "evals_per_search_algorithmic": dg["evals_alg"] / max(dg["searches"], 1),
         "evals_per_search_made": dg["evals_dedup"] / max(dg["searches"], 1),
@@ -1259,8 +1289,47 @@ def run_diff(args, embedded=False, pk=None):
     return line
 
 
+def run_launch_list(args):
+    """Two direct (uncaptured) steps, no timing: the second step's kernels are the ones
+    a launch list or a per-kernel capture takes (skip the first step's launches)."""
+    import torch
+    from paper_2509_26193_gb300 import build, relearn as R
+    build.build()
+    device = torch.device("cuda", torch.cuda.current_device())
+    if args.workload == "batch":
+        run = BatchRunner(batch_workload(args.networks), device)
+        step = run.step
+    elif args.workload == "diff":
+        from paper_2509_26193_gb300 import workloads
+        from paper_2509_26193_gb300.differentiable import mean_synapse_length
+        net = workloads.differentiable_cube()
+        d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        x, y, z = (d(a).requires_grad_(True) for a in (net.x, net.y, net.z))
+        va, vd = d(net.vac_ax), d(net.vac_de)
+        sigma = torch.tensor([net.sigma], dtype=torch.float32, device=device,
+                             requires_grad=True)
+        ctx = R.relearn_create(net.n, 64)
+
+        def step():
+            mean_synapse_length(ctx, x, y, z, sigma, va, vd, net.theta).backward()
+    else:
+        run = Runner(workload(args.n), args.theta, device, args.group,
+                     R.FLAG_REGROUP if args.regroup else 0)
+        step = lambda: run.step(timing=False)
+    counts = []
+    for _ in range(2):
+        l0 = R.relearn_launch_count()
+        step()
+        torch.cuda.synchronize()
+        counts.append(R.relearn_launch_count() - l0)
+    print(json.dumps({"launch_list": args.workload, "launches_per_step": counts}), flush=True)
+
+
 def main():
     args = parse()
+    if args.launch_list:
+        run_launch_list(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":

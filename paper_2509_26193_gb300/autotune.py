@@ -1,12 +1,14 @@
 """Autotuner of the search kernel's launch-time knob.
 
-The search kernel walks the octree with groups of source neurons (``search_group``
-in relearn_params): 32 or 8 neurons that are close in Morton order share one walk,
-or every lane walks alone; the default picks the width per warp from the Morton
-spread of the warp's sources, with two depth thresholds. The best thresholds
-depend on the workload (cluster sizes, density, sigma relative to the domain).
-Results never depend on the choice, only the time does, so the tuner simply
-times each candidate on the caller's own update and keeps the fastest.
+The search kernel walks the octree with unions of source neurons that are adjacent
+in Morton order (``search_group`` in relearn_params). By default each warp's 32
+sources are cut into pieces wherever two neighbours do not share a cell of some
+cut depth, and each piece walks one union; the cut depth follows the share of
+neurons that search. A fixed width (32, 8, or every lane alone) or another cut depth
+can be forced. The best choice depends on the workload (cluster sizes, density,
+sigma relative to the domain). Results never depend on the choice, only the time
+does, so the tuner simply times each candidate on the caller's own update and keeps
+the fastest.
 
 The tuner runs trials through a caller-supplied function that performs one
 update with the given ``search_group`` and returns the search kernel's device

@@ -93,12 +93,13 @@ void free_all(relearn_ctx *c)
         (void **)&c->d_prio_ax,  (void **)&c->d_prio_de,
         (void **)&c->d_sel_ax,   (void **)&c->d_sel_de,     (void **)&c->d_need_ax,
         (void **)&c->d_need_de,  (void **)&c->d_keep,       (void **)&c->scan.block_sums,
-        (void **)&c->sort.hist};
+        (void **)&c->scan.flags, (void **)&c->sort.hist};
     for (void **p : ptrs) {
         if (*p) cudaFree(*p);
         *p = nullptr;
     }
     c->sort.scan.block_sums = nullptr;
+    c->sort.scan.flags = nullptr;
     if (c->h_off) cudaFreeHost(c->h_off);
     c->h_off = nullptr;
     if (c->off_ev) cudaEventDestroy(c->off_ev);
@@ -269,10 +270,12 @@ relearn_status relearn_create_batched(relearn_ctx **out, int device, int64_t max
     A(sort.hist, 256 * sort_blocks);
     int64_t scan_blocks = std::max({scan_blocks_needed(N + 1), scan_blocks_needed(QC),
                                     scan_blocks_needed(S), scan_blocks_needed(256 * sort_blocks)});
-    A(scan.block_sums, scan_blocks + 1);
+    A(scan.block_sums, 2 * scan_blocks);
+    A(scan.flags, scan_blocks + 3);
 #undef A
     if (e == cudaSuccess) {
         c->scan.max_blocks = scan_blocks;
+        c->scan.status = c->d_status;
         c->sort.max_blocks = sort_blocks;
         c->sort.scan = c->scan;
         for (cudaEvent_t &ev : c->ev)
@@ -284,6 +287,8 @@ relearn_status relearn_create_batched(relearn_ctx **out, int device, int64_t max
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_off, (NB + 1) * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->off_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = cudaMemset(c->scan.flags, 0, (c->scan.max_blocks + 3) * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->d_i64, 0, 16 * sizeof(int64_t));
     if (e == cudaSuccess) e = cudaMemset(c->d_i32, 0, 32 * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -101,6 +101,7 @@ __device__ __forceinline__ void load_node(const Node *n, float4 &g, int2 &t)
 
 constexpr int kMaxDepth = 10;
 
+
 // Number of leading octal digits (octree levels) two Morton codes share; 10 when equal.
 __device__ __forceinline__ int morton_common_digits(uint32_t a, uint32_t b)
 {

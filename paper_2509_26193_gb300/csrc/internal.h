@@ -9,9 +9,12 @@
 
 namespace rl {
 
-// Scratch of the device-wide exclusive scan (two-level, int64 block sums).
+// Scratch of the device-wide single-pass exclusive scan.
 struct ScanScratch {
-    int64_t *block_sums = nullptr; // [max_blocks + 1]
+    int64_t *block_sums = nullptr; // [2 * max_blocks]: tile sums, then inclusive prefixes
+    int32_t *flags = nullptr;      // [max_blocks + 3]: ticket, abort, blocks done, tile
+                                   // states; zero between scans
+    int32_t *status = nullptr;     // device status word for a wait that ran out (or NULL)
     int64_t max_blocks = 0;
 };
 
@@ -45,7 +48,8 @@ struct SearchConst {
 struct relearn_ctx {
     int device = 0;
     int num_sms = 0;
-    int search_occ[2][2] = {{0, 0}, {0, 0}}; // resident blocks per SM: [batched][union, split]
+    // resident blocks per SM: [2 * batched + diagnostics][union, split]
+    int search_occ[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     int64_t max_neurons = 0, max_synapses = 0, max_searches = 0, max_nodes = 0;
     int32_t max_nets = 1; // networks one build may hold
     int32_t num_nets = 1; // networks in the current tree
@@ -139,7 +143,7 @@ struct relearn_ctx {
 // slots of d_i64 / d_i32
 enum { I64_Q = 0, I64_FAILED, I64_DECLINED, I64_FORMED, I64_NSYN, I64_BROKEN, I64_SCAN_TOTAL,
        I64_NODES, I64_Q_TOTAL, I64_EVALS_TOTAL, I64_ACTIVE, I64_STEPS_TOTAL, I64_LEN_EVALS };
-enum { I32_N = 0, I32_Q, I32_NSYN, I32_NEW, I32_NODES, I32_WORK, I32_ACTIVE, I32_RQ };
+enum { I32_N = 0, I32_Q, I32_NSYN, I32_NEW, I32_NODES, I32_WORK, I32_ACTIVE, I32_RQ, I32_BASE };
 
 namespace rl {
 

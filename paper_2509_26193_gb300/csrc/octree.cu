@@ -95,6 +95,49 @@ __global__ void bbox_kernel(const float *__restrict__ x, const float *__restrict
     }
 }
 
+// One network: every thread folds its elements into a running min / max, then the
+// block reduces (warp shuffles, then shared memory) and issues six atomics, instead
+// of six per warp and grid stride.
+__global__ void __launch_bounds__(256) bbox_one_kernel(const float *__restrict__ x,
+                                                       const float *__restrict__ y,
+                                                       const float *__restrict__ z, int64_t n,
+                                                       uint32_t *d_ord)
+{
+    __shared__ uint32_t s_red[8][6];
+    uint32_t v[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float p[3] = {x[i], y[i], z[i]};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (p[a] == p[a]) {
+                const uint32_t o = ordered(p[a]);
+                v[a] = min(v[a], o);
+                v[3 + a] = max(v[3 + a], o);
+            }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o; o >>= 1) {
+            v[a] = min(v[a], __shfl_xor_sync(0xffffffffu, v[a], o));
+            v[3 + a] = max(v[3 + a], __shfl_xor_sync(0xffffffffu, v[3 + a], o));
+        }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int a = 0; a < 6; ++a) s_red[w][a] = v[a];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int a = threadIdx.x;
+        uint32_t r = s_red[0][a];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
+            r = a < 3 ? min(r, s_red[k][a]) : max(r, s_red[k][a]);
+        if (a < 3)
+            atomicMin(&d_ord[a], r);
+        else
+            atomicMax(&d_ord[a], r);
+    }
+}
+
 // Also writes the offsets {0, n} of a single network when off_one is given.
 __global__ void bbox_init_kernel(uint32_t *d_ord, int32_t B, int64_t *off_one, int64_t n)
 {
@@ -618,7 +661,10 @@ cudaError_t octree_build(relearn_ctx *c, int64_t n, int32_t B, const float *x, c
     const unsigned gb = (unsigned)((B + 255) / 256);
     bbox_init_kernel<<<gb, 256, 0, st>>>(c->d_ord, B, B == 1 ? c->d_off : nullptr, n);
     note_launch();
-    bbox_kernel<<<gn, 256, 0, st>>>(x, y, z, n, c->d_off, B, c->d_ord);
+    if (B == 1)
+        bbox_one_kernel<<<gn, 256, 0, st>>>(x, y, z, n, c->d_ord);
+    else
+        bbox_kernel<<<gn, 256, 0, st>>>(x, y, z, n, c->d_off, B, c->d_ord);
     note_launch();
     geom_kernel<<<gb, 256, 0, st>>>(c->d_ord, box, c->d_geom, B);
     note_launch();
@@ -712,7 +758,9 @@ cudaError_t octree_reduce(relearn_ctx *c, const int32_t *vac_de, cudaStream_t st
 // loads this library keeps it until the process exits. All calls on a device
 // share it and it keeps the previous call's contents, so calls whose GPU work
 // overlaps (different streams, no ordering between them) race on it. Nothing in
-// it has to start at zero except the box words, which every call resets.
+// it has to start at zero except the box words, which every call resets, and the
+// scans' tile states, which start at zero (static storage) and which every scan
+// clears again when it finishes.
 // ---------------------------------------------------------------------------
 namespace rl {
 namespace {
@@ -725,7 +773,9 @@ constexpr size_t kOffCodesAlt = 512;
 constexpr size_t kOffPermAlt = kOffCodesAlt + 4 * size_t(kNoAllocMaxN);
 constexpr size_t kOffHist = kOffPermAlt + 4 * size_t(kNoAllocMaxN);
 constexpr size_t kOffScan = kOffHist + 4 * 256 * size_t(kNoAllocSortBlocks);
-constexpr size_t kNoAllocBytes = kOffScan + 8 * size_t(kNoAllocScanBlocks + 1);
+constexpr size_t kOffScanFlags = kOffScan + 8 * 2 * size_t(kNoAllocScanBlocks);
+constexpr size_t kOffStatus = kOffScanFlags + 4 * size_t(kNoAllocScanBlocks + 3);
+constexpr size_t kNoAllocBytes = kOffStatus + 4;
 // the regions must not overlap: the box words (6 x uint32) below the geometry, the
 // geometry below the sort's ping-pong buffers; 8-byte sums on 8-byte boundaries
 static_assert(6 * sizeof(uint32_t) <= kOffGeom, "box words overlap the geometry");
@@ -797,6 +847,9 @@ extern "C" relearn_status relearn_morton_order_noalloc(int64_t n, const float *x
     ss.hist = reinterpret_cast<int32_t *>(d.base + kOffHist);
     ss.max_blocks = kNoAllocSortBlocks;
     ss.scan.block_sums = reinterpret_cast<int64_t *>(d.base + kOffScan);
+    ss.scan.flags = reinterpret_cast<int32_t *>(d.base + kOffScanFlags);
+    // a scan wait that runs out (it cannot: every wait ends) would be recorded here
+    ss.scan.status = reinterpret_cast<int32_t *>(d.base + kOffStatus);
     ss.scan.max_blocks = kNoAllocScanBlocks;
     cudaStream_t st = (cudaStream_t)stream;
     Box box{};
@@ -810,7 +863,7 @@ extern "C" relearn_status relearn_morton_order_noalloc(int64_t n, const float *x
     // One network: the box and Morton kernels never read the network offsets.
     bbox_init_kernel<<<1, 32, 0, st>>>(ord, 1, nullptr, n); // geom_kernel reads the box
     note_launch();
-    bbox_kernel<<<grid, 256, 0, st>>>(x, y, z, n, nullptr, 1, ord);
+    bbox_one_kernel<<<grid, 256, 0, st>>>(x, y, z, n, ord);
     note_launch();
     geom_kernel<<<1, 1, 0, st>>>(ord, box, geom, 1);
     note_launch();

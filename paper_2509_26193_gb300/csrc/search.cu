@@ -16,7 +16,9 @@
 // node is loaded once per union (one broadcast load), and each lane still meets
 // exactly its own candidates in Morton order, which is the order of the
 // cumulative draw. Every kCkStride union steps each lane stores a checkpoint
-// (its next own node, its running sum).
+// (its next own node, its running sum); when the list is full, every other
+// checkpoint is dropped and checkpoints are stored half as often, so a draw never
+// walks more than one interval however long the walk.
 //
 // Updates with few sources run bh_split_kernel instead (one warp per source, its
 // frontier walk shared out among the lanes; see there).
@@ -42,8 +44,8 @@ namespace rl {
 
 namespace {
 
-constexpr int kCkStride = 128; // warp steps between checkpoints
-constexpr int kMaxCk = 128;    // checkpoints kept per lane (later steps reuse the last one)
+constexpr int kCkStride = 128; // warp steps between checkpoints (times 2^k once the list fills)
+constexpr int kMaxCk = 128;    // checkpoints kept per lane
 constexpr float kTiny = 8.673617e-19f; // 2^-60
 // Walks per warp (see bh_search_kernel): the warp's 32 sources are cut into pieces
 // at the boundaries of cells of some depth, and each piece walks one union. When
@@ -64,13 +66,12 @@ constexpr int kSplitWaves = 9;
 
 // A node of depth d is accepted iff d^2 > thr0 / 4^d, thr0 = (root length / theta)^2
 // rounded to FP32 (see NodeTopo::shift). theta = 0 accepts no inner node.
-// One thread per network; per-network sigma/theta replace the scalars when given.
-__global__ void search_const_kernel(const Geom *g_all, int32_t B, float sigma, float theta,
-                                    const float *net_sigma, const float *net_theta,
-                                    SearchConst *sc_all, int32_t *status)
+// Network b's constants; per-network sigma/theta replace the scalars when given.
+__device__ __forceinline__ void search_const_one(int32_t b, const Geom *g_all, float sigma,
+                                                 float theta, const float *net_sigma,
+                                                 const float *net_theta, SearchConst *sc_all,
+                                                 int32_t *status)
 {
-    const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
     float sg = net_sigma ? net_sigma[b] : sigma;
     float tt = net_theta ? net_theta[b] : theta;
     if (!(sg > 0.0f && sg < 3.0e38f && tt >= 0.0f && tt < 3.0e38f)) {
@@ -88,13 +89,31 @@ __global__ void search_const_kernel(const Geom *g_all, int32_t B, float sigma, f
     sc->pad = 0.0f;
 }
 
+// One thread per network.
+__global__ void search_const_kernel(const Geom *g_all, int32_t B, float sigma, float theta,
+                                    const float *net_sigma, const float *net_theta,
+                                    SearchConst *sc_all, int32_t *status)
+{
+    const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) search_const_one(b, g_all, sigma, theta, net_sigma, net_theta, sc_all, status);
+}
+
 // active[s] = 1 if the neuron at Morton position s has vacant axonal elements;
-// cnt_id[i] = its number of searches (canonical request order is by id).
+// cnt_id[i] = its number of searches (canonical request order is by id). Thread b < B
+// also forms network b's search constants (as search_const_kernel; the grid covers B
+// since every network holds a neuron).
 __global__ void query_counts_kernel(const int32_t *__restrict__ vac_ax,
                                     const int32_t *__restrict__ perm, int64_t n,
-                                    int32_t *__restrict__ active, int32_t *__restrict__ cnt_id)
+                                    int32_t *__restrict__ active, int32_t *__restrict__ cnt_id,
+                                    const Geom *g_all, int32_t B, float sigma, float theta,
+                                    const float *net_sigma, const float *net_theta,
+                                    SearchConst *sc_all, int32_t *status)
 {
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= n;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid < B)
+        search_const_one((int32_t)tid, g_all, sigma, theta, net_sigma, net_theta, sc_all,
+                         status);
+    for (int64_t s = tid; s <= n;
          s += (int64_t)gridDim.x * blockDim.x) {
         if (s == n) {
             active[n] = 0;
@@ -107,33 +126,30 @@ __global__ void query_counts_kernel(const int32_t *__restrict__ vac_ax,
     }
 }
 
-// Q = total searches; beyond capacity the update is void (status CAPACITY), and so
-// it is while an earlier device error (e.g. a bad per-network parameter) is unread.
-__global__ void query_check_kernel(const int64_t *d_total, const int64_t *d_active,
-                                   int64_t max_searches, int32_t *d_Q, int32_t *d_A,
-                                   int64_t *d_Qout, int64_t *d_Qsum, int32_t *status)
-{
-    int64_t q = *d_total;
-    int64_t a = *d_active;
-    *d_Qout = q;
-    if (q > max_searches) set_status(status, RELEARN_ERR_CAPACITY);
-    if (*(volatile int32_t *)status != 0) {
-        q = 0;
-        a = 0;
-    }
-    *d_Q = (int32_t)q;
-    *d_A = (int32_t)a;
-    *d_Qsum += q;
-}
-
+// Q = total searches; beyond capacity the update is void (status CAPACITY), and so it
+// is while an earlier device error (e.g. a bad per-network parameter) is unread. Every
+// block forms the same Q from the same totals; block 0 publishes it. Then the source
+// list (Morton order) and the request records (id order) are filled.
 __global__ void query_fill_kernel(const int32_t *__restrict__ vac_ax, int64_t n,
                                   const int32_t *__restrict__ active,
                                   const int32_t *__restrict__ act_off,
-                                  const int32_t *__restrict__ qoff_o, const int32_t *d_Q,
+                                  const int32_t *__restrict__ qoff_o, const int64_t *d_total,
+                                  const int64_t *d_active, int64_t max_searches, int32_t *d_Q,
+                                  int32_t *d_A, int64_t *d_Qout, int64_t *d_Qsum, int32_t *status,
                                   int32_t *__restrict__ act_src, int32_t *__restrict__ req_src,
                                   int32_t *__restrict__ req_elem, int32_t *__restrict__ req_tgt)
 {
-    if (*d_Q == 0) return;
+    const int64_t q = *d_total;
+    const bool over = q > max_searches;
+    const bool void_ = over || *(volatile int32_t *)status != 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *d_Qout = q;
+        if (over) set_status(status, RELEARN_ERR_CAPACITY);
+        *d_Q = void_ ? 0 : (int32_t)q;
+        *d_A = void_ ? 0 : (int32_t)*d_active;
+        *d_Qsum += void_ ? 0 : q;
+    }
+    if (void_) return;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
          s += (int64_t)gridDim.x * blockDim.x) {
         if (active[s]) act_src[act_off[s]] = (int32_t)s;
@@ -341,6 +357,17 @@ __device__ __forceinline__ int32_t restart_chain(const SearchArgs &a, int32_t k,
     return -1;
 }
 
+// Keep every other checkpoint (the list is full). Not inlined: it runs at most a few
+// times per long walk and keeps its registers out of the walk loop.
+__device__ __noinline__ void ck_halve(int32_t *ckp, float *ckc, float *ckk)
+{
+    for (int j = 0; j < kMaxCk / 2; ++j) {
+        ckp[j] = ckp[2 * j];
+        ckc[j] = ckc[2 * j];
+        ckk[j] = ckk[2 * j];
+    }
+}
+
 // Deferred restart: queue search `out` of the source at Morton position s with
 // its first draw k (warp-aggregated slot allocation).
 __device__ __forceinline__ void enqueue_restart(const SearchArgs &a, int32_t k, int32_t out,
@@ -469,17 +496,29 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
         for (int attempt = 0; attempt < 2; ++attempt) {
             int32_t p = root + 1, skip = live ? 0 : 0x7fffffff, steps = 0;
             float cum = 0.0f, comp = 0.0f; // Kahan sum and compensation
+            int32_t ckst = 0; // checkpoints stored (bits 0-7) and log2 of the interval in
+                              // blocks (bits 8-15): no further live register in the walk
             own = 0;
-            nck = 0;
+            // at the start of each block (`steps` is then a multiple of kCkStride): a
+            // checkpoint every 2^(ckst >> 8) blocks; when the list is full keep every other
+            // one and store half as often (walks of more than kMaxCk * kCkStride steps)
+            auto checkpoint = [&](int32_t at) {
+                if (((steps / kCkStride) & ((1 << (ckst >> 8)) - 1)) != 0) return;
+                int32_t k = ckst & 0xff;
+                if (k == kMaxCk) {
+                    ck_halve(ckp, ckc, ckk);
+                    k = kMaxCk / 2;
+                    ckst += 1 << 8;
+                }
+                ckp[k] = at;
+                ckc[k] = cum;
+                ckk[k] = comp;
+                ckst = (ckst & ~0xff) | (k + 1);
+            };
             if (G == 32) {
                 // one walk per warp: every lane steps together, no group masks
                 while (p < root_end) {
-                    if (nck < kMaxCk) {
-                        ckp[nck] = max(p, skip);
-                        ckc[nck] = cum;
-                        ckk[nck] = comp;
-                        ++nck;
-                    }
+                    checkpoint(max(p, skip));
                     int k = 0;
                     if constexpr (!kBatched) {
                         // four steps per test: nodes root_end .. root_end + 2 are
@@ -507,12 +546,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
                     int2 t = make_int2(p + 1, 0);
                     if (run) {
-                        if ((steps & (kCkStride - 1)) == 0 && nck < kMaxCk) {
-                            ckp[nck] = max(p, skip);
-                            ckc[nck] = cum;
-                            ckk[nck] = comp;
-                            ++nck;
-                        }
+                        if ((steps & (kCkStride - 1)) == 0) checkpoint(max(p, skip));
                         ++steps;
                         g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[p].g));
                         t = __ldg(reinterpret_cast<const int2 *>(&a.nodes[p].t));
@@ -531,6 +565,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                 }
             }
             if (lane == seg_first) my_steps += steps; // one count per walk
+            nck = ckst & 0xff;
             S = (double)cum - (double)comp;
             // every term underflowed: redo with the exponents shifted by the nearest d^2
             const bool redo = live && S < (double)kTiny;
@@ -964,10 +999,11 @@ cudaError_t search_prepare(relearn_ctx *c, const relearn_params &p, const int32_
 {
     cudaError_t e;
     const int64_t n = c->n;
-    if ((e = search_constants(c, p, st))) return e;
     int32_t *active = c->d_cnt, *cnt_o = c->d_tcnt; // scratch
-    query_counts_kernel<<<grid_for(n + 1, 256, c->num_sms), 256, 0, st>>>(vac_ax, c->d_perm, n,
-                                                                          active, cnt_o);
+    // grid_for(n + 1) threads cover every network: each holds at least one neuron
+    query_counts_kernel<<<grid_for(n + 1, 256, c->num_sms), 256, 0, st>>>(
+        vac_ax, c->d_perm, n, active, cnt_o, c->d_geom, c->num_nets, p.sigma, p.theta,
+        p.net_sigma, p.net_theta, c->d_sc, c->d_status);
     note_launch();
     if ((e = scan_exclusive(active, c->d_act_off, n + 1, nullptr, c->d_i64 + I64_ACTIVE, c->scan,
                             st)))
@@ -975,13 +1011,11 @@ cudaError_t search_prepare(relearn_ctx *c, const relearn_params &p, const int32_
     if ((e = scan_exclusive(cnt_o, c->d_qoff_o, n + 1, nullptr, c->d_i64 + I64_SCAN_TOTAL,
                             c->scan, st)))
         return e;
-    query_check_kernel<<<1, 1, 0, st>>>(c->d_i64 + I64_SCAN_TOTAL, c->d_i64 + I64_ACTIVE,
-                                        c->max_searches, c->d_i32 + I32_Q, c->d_i32 + I32_ACTIVE,
-                                        c->d_i64 + I64_Q, c->d_i64 + I64_Q_TOTAL, c->d_status);
-    note_launch();
     query_fill_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(
-        vac_ax, n, active, c->d_act_off, c->d_qoff_o, c->d_i32 + I32_Q, c->d_act_src,
-        c->d_req_src, c->d_req_elem, c->d_req_tgt);
+        vac_ax, n, active, c->d_act_off, c->d_qoff_o, c->d_i64 + I64_SCAN_TOTAL,
+        c->d_i64 + I64_ACTIVE, c->max_searches, c->d_i32 + I32_Q, c->d_i32 + I32_ACTIVE,
+        c->d_i64 + I64_Q, c->d_i64 + I64_Q_TOTAL, c->d_status, c->d_act_src, c->d_req_src,
+        c->d_req_elem, c->d_req_tgt);
     note_launch();
     return cudaGetLastError();
 }

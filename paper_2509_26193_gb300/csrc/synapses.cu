@@ -77,7 +77,8 @@ __global__ void accept_decide_kernel(const int32_t *d_Q, const int32_t *__restri
                                      const int32_t *__restrict__ toff,
                                      const int32_t *__restrict__ bucket,
                                      const int32_t *__restrict__ vac_de,
-                                     uint8_t *__restrict__ acc, int64_t *declined)
+                                     uint8_t *__restrict__ acc, int32_t *__restrict__ flag,
+                                     int64_t *declined)
 {
     const int64_t Q = *d_Q;
     int64_t dec = 0;
@@ -105,6 +106,7 @@ __global__ void accept_decide_kernel(const int32_t *d_Q, const int32_t *__restri
             dec += a ? 0 : 1;
         }
         acc[r] = a;
+        flag[r] = a; // scanned by the apply step into the new synapses' positions
     }
     for (int off = 16; off; off >>= 1) dec += __shfl_xor_sync(0xffffffffu, dec, off);
     if ((threadIdx.x & 31) == 0 && dec)
@@ -112,30 +114,30 @@ __global__ void accept_decide_kernel(const int32_t *d_Q, const int32_t *__restri
 }
 
 // ---------------------------------------------------------------- apply
-__global__ void flags_kernel(const int32_t *d_Q, const uint8_t *__restrict__ acc,
-                             int32_t *__restrict__ out)
-{
-    const int64_t Q = *d_Q;
-    GRID_STRIDE(r, Q) out[r] = acc[r];
-}
-
-// New store size check: formed = *d_formed; nothing is applied on overflow.
+// New store size check: formed = *d_formed; nothing is applied on overflow. The
+// store grows here: the apply kernel writes the new synapses from *d_base (the old
+// size) on.
 __global__ void apply_check_kernel(const int64_t *d_formed, int32_t *d_nsyn, int32_t *d_new,
-                                   int64_t max_synapses, int32_t *status, int64_t *d_formed_out)
+                                   int32_t *d_base, int64_t *d_nsyn64, int64_t max_synapses,
+                                   int32_t *status, int64_t *d_formed_out)
 {
     int64_t f = *d_formed;
+    const int32_t base = *d_nsyn;
     const bool failed = *(volatile int32_t *)status != 0; // an earlier kernel reported an error
-    if (failed || (int64_t)*d_nsyn + f > max_synapses) {
+    *d_base = base;
+    if (failed || (int64_t)base + f > max_synapses) {
         if (!failed) set_status(status, RELEARN_ERR_CAPACITY);
         *d_new = -1;
         *d_formed_out = 0;
     } else {
         *d_new = (int32_t)f;
         *d_formed_out = f;
+        *d_nsyn = base + (int32_t)f;
     }
+    *d_nsyn64 = *d_nsyn;
 }
 
-__global__ void apply_kernel(const int32_t *d_Q, const int32_t *d_new, const int32_t *d_nsyn,
+__global__ void apply_kernel(const int32_t *d_Q, const int32_t *d_new, const int32_t *d_base,
                              const int32_t *__restrict__ req_src,
                              const int32_t *__restrict__ req_tgt, const uint8_t *__restrict__ acc,
                              const int32_t *__restrict__ newpos, const uint8_t *__restrict__ type,
@@ -144,7 +146,7 @@ __global__ void apply_kernel(const int32_t *d_Q, const int32_t *d_new, const int
 {
     if (*d_new < 0) return;
     const int64_t Q = *d_Q;
-    const int32_t base = *d_nsyn;
+    const int32_t base = *d_base;
     GRID_STRIDE(r, Q)
     {
         if (!acc[r]) continue;
@@ -156,12 +158,6 @@ __global__ void apply_kernel(const int32_t *d_Q, const int32_t *d_new, const int
         syn_tgt[k] = t;
         syn_sign[k] = type[s] ? (int8_t)-1 : (int8_t)1;
     }
-}
-
-__global__ void grow_store_kernel(const int32_t *d_new, int32_t *d_nsyn, int64_t *d_nsyn64)
-{
-    if (*d_new > 0) *d_nsyn += *d_new;
-    *d_nsyn64 = *d_nsyn;
 }
 
 // ---------------------------------------------------------------- store
@@ -391,7 +387,8 @@ cudaError_t accept_requests(relearn_ctx *c, const relearn_params &p, const int32
     note_launch();
     accept_decide_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_src, c->d_req_elem, c->d_req_tgt,
                                              c->d_req_prio, c->d_tcnt, c->d_toff, c->d_bucket,
-                                             vac_de, c->d_req_acc, c->d_i64 + I64_DECLINED);
+                                             vac_de, c->d_req_acc, c->d_newpos,
+                                             c->d_i64 + I64_DECLINED);
     note_launch();
     return cudaGetLastError();
 }
@@ -448,21 +445,18 @@ cudaError_t apply_requests(relearn_ctx *c, int32_t *vac_ax, int32_t *vac_de, con
     cudaError_t e;
     const int32_t *dQ = c->d_i32 + I32_Q;
     const unsigned gq = grid_for(c->max_searches, 256, c->num_sms);
-    flags_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_acc, c->d_newpos);
-    note_launch();
+    // d_newpos holds the acceptance flags (written by the acceptance step)
     if ((e = scan_exclusive(c->d_newpos, c->d_newpos, c->max_searches, dQ,
                             c->d_i64 + I64_SCAN_TOTAL, c->scan, st)))
         return e;
     apply_check_kernel<<<1, 1, 0, st>>>(c->d_i64 + I64_SCAN_TOTAL, c->d_i32 + I32_NSYN,
-                                        c->d_i32 + I32_NEW, c->max_synapses, c->d_status,
+                                        c->d_i32 + I32_NEW, c->d_i32 + I32_BASE,
+                                        c->d_i64 + I64_NSYN, c->max_synapses, c->d_status,
                                         c->d_i64 + I64_FORMED);
     note_launch();
-    apply_kernel<<<gq, 256, 0, st>>>(dQ, c->d_i32 + I32_NEW, c->d_i32 + I32_NSYN, c->d_req_src,
+    apply_kernel<<<gq, 256, 0, st>>>(dQ, c->d_i32 + I32_NEW, c->d_i32 + I32_BASE, c->d_req_src,
                                      c->d_req_tgt, c->d_req_acc, c->d_newpos, type, vac_ax,
                                      vac_de, c->d_syn_src, c->d_syn_tgt, c->d_syn_sign);
-    note_launch();
-    grow_store_kernel<<<1, 1, 0, st>>>(c->d_i32 + I32_NEW, c->d_i32 + I32_NSYN,
-                                       c->d_i64 + I64_NSYN);
     note_launch();
     // new synapses sit unsorted at the end of the store until an operation needs the
     // canonical order (deletion, export); spike delivery reads the store in any order
