@@ -1216,7 +1216,9 @@ def run_diff(args, embedded=False, pk=None):
         u2, s2 = aggregate(units_per_step * args.steps, ms2 / 1000.0, ws, device)
         e2e = {"value": u2 / s2, "unit": UNIT, "h2d_bytes_per_step": 20 * net.n,
                "d2h_bytes_per_step": 12 * net.n, "clocks": clk2}
-    # sigma calibration: 50 Adam steps toward a 600 um mean length
+    # sigma calibration: 50 Adam steps toward a 600 um mean length (two untimed steps
+    # first: the first optimizer step of a process pays a one-time start-up cost)
+    calibrate_sigma(ctx, x.detach(), y.detach(), z.detach(), va, vd, net.sigma, 600.0, steps=2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sig, means = calibrate_sigma(ctx, x.detach(), y.detach(), z.detach(), va, vd, net.sigma,
