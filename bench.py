@@ -404,19 +404,22 @@ class Runner:
         self.vac_ax.copy_(self.vac_ax0)
         self.vac_de.copy_(self.vac_de0)
         R.relearn_build_octree(self.ctx, self.x, self.y, self.z)
-        q0, e0, _ = self.counters()
+        q0, e0, w0 = self.counters()
         evals = 0
         for u in range(UPDATES_PER_STEP):
             p = R.params(self.net.sigma, self.theta, self.net.seed, 500000 + u,
                          R.FLAG_DIAG | self.extra_flags, self.group)
             R.relearn_update_connectivity(self.ctx, p, self.vac_ax, self.vac_de, self.type)
             evals += int(R.relearn_get_search_diag(self.ctx)["evals"].astype(np.int64).sum())
-        q1, e1, _ = self.counters()
+        q1, e1, w1 = self.counters()
         p = R.params(self.net.sigma, self.theta, self.net.seed, 500999)
         R.relearn_delete_synapses(self.ctx, p, self.retract, self.retract, self.vac_ax,
                                   self.vac_de)
         self.torch.cuda.synchronize()
-        return {"searches": q1 - q0, "evals_alg": evals, "evals_dedup": e1 - e0}
+        # the library counts evaluations and walk steps only in counted (here: diagnostic)
+        # updates; the timed steps run uncounted
+        return {"searches": q1 - q0, "evals_alg": evals, "evals_dedup": e1 - e0,
+                "walk_steps": w1 - w0}
 
     def build_graph_ms(self, reps=20):
         """The octree build (a1-a3) alone, captured in a CUDA graph and replayed: its
@@ -464,7 +467,7 @@ class Runner:
         torch = self.torch
         st = torch.cuda.current_stream()
         total_ms = 0.0
-        q0, e0, w0 = self.counters()
+        q0 = self.counters()[0]
         for _ in range(steps):
             self.flush.zero_()
             torch.cuda.synchronize()
@@ -479,14 +482,13 @@ class Runner:
             b.record(st)
             torch.cuda.synchronize()
             total_ms += a.elapsed_time(b)
-        q1, e1, w1 = self.counters()
-        return {"ms": total_ms, "searches": q1 - q0, "evals": e1 - e0, "walk_steps": w1 - w0}
+        return {"ms": total_ms, "searches": self.counters()[0] - q0}
 
     def timed(self, steps, e2e):
         torch = self.torch
         st = torch.cuda.current_stream()
         total_ms = 0.0
-        q0, e0, w0 = self.counters()
+        q0 = self.counters()[0]
         self.R.relearn_collect_search_times(self.ctx)
         k_ms, k_n = 0.0, 0
         l0 = self.R.relearn_launch_count()
@@ -504,9 +506,7 @@ class Runner:
             k_ms += ms
             k_n += kn
         launches = self.R.relearn_launch_count() - l0
-        q1, e1, w1 = self.counters()
-        return {"ms": total_ms, "searches": q1 - q0, "evals": e1 - e0, "walk_steps": w1 - w0,
-                "kernel_ms": k_ms,
+        return {"ms": total_ms, "searches": self.counters()[0] - q0, "kernel_ms": k_ms,
                 "kernel_launches": k_n, "launches": launches}
 
 
@@ -671,8 +671,9 @@ def measure_clusters(net, theta, device, args, pk, counters, regroup=False, e2e=
     # work of the timed region: the oracle-basis evaluations per search (diagnostics
     # step) x the region's searches; expansions from the oracle's ratio X / E (xe)
     evals_alg = dg["evals_alg"] / max(dg["searches"], 1) * res["searches"]
+    evals_made = dg["evals_dedup"] / max(dg["searches"], 1) * res["searches"]
     out["roofline"] = search_roofline(
-        res["kernel_ms"], res["kernel_launches"], evals_alg, res["evals"],
+        res["kernel_ms"], res["kernel_launches"], evals_alg, evals_made,
         (xe or 0.0) * evals_alg, pk, counters,
         "search (bh_search_kernel + bh_split_kernel, one launch pair per update)")
     if xe is None:
@@ -740,7 +741,7 @@ def run_ours(args):
         "execution": "one CUDA graph replay per step" if args.graph else
                      "direct calls (one C-ABI call per operation)",
         "launches_per_step": res["launches"] / args.steps,
-        "walk_steps_per_search": res["walk_steps"] / max(res["searches"], 1),
+        "walk_steps_per_search": dg["walk_steps"] / max(dg["searches"], 1),
         "parity_sample": parity_sample(prof["targets"], orc_sample),
         "alu_peaks": pk}
     line = {"metric": METRIC, "value": units / secs, "unit": UNIT, "n_gpus": ws,
@@ -884,7 +885,7 @@ class BatchRunner:
         torch = self.torch
         st = torch.cuda.current_stream()
         total = 0.0
-        q0, e0 = self.counters()
+        q0 = self.counters()[0]
         l0 = self.R.relearn_launch_count()
         for _ in range(steps):
             self.flush.zero_()
@@ -903,8 +904,7 @@ class BatchRunner:
             c.record(st)
             torch.cuda.synchronize()
             total += a.elapsed_time(c)
-        q1, e1 = self.counters()
-        return {"ms": total, "searches": q1 - q0, "evals": e1 - e0,
+        return {"ms": total, "searches": self.counters()[0] - q0,
                 "launches_host": self.R.relearn_launch_count() - l0}
 
     def h2d_bytes(self):

@@ -103,6 +103,11 @@ typedef struct {
  * separate kernel in which neighbouring threads restart inside the same subtree. Results
  * are bit-identical to the default (restarts finished inline by the lane that drew). */
 #define RELEARN_FLAG_REGROUP 4u
+/* Count node evaluations and walk steps into evals_total / walk_steps_total of
+ * relearn_update_stats (RELEARN_FLAG_DIAG counts as well). Counting costs about one
+ * instruction per step of the search walks (a few per cent of the search time), so
+ * updates run without either flag add nothing to those totals. */
+#define RELEARN_FLAG_COUNT 8u
 
 /* Host-side summary of one update (filled when a stats pointer is passed; this
  * synchronises the stream). Times are CUDA-event milliseconds. */
@@ -118,8 +123,9 @@ typedef struct {
     float ms_accept, ms_apply, ms_total;
     int32_t reserved;
     int64_t searches_total;     /* searches of every update since the context was created */
-    int64_t evals_total;        /* node evaluations (count > 0) of those searches: the
-                                   algorithmic work of the search, one per frontier candidate */
+    int64_t evals_total;        /* node evaluations (count > 0) of the searches of updates run
+                                   with RELEARN_FLAG_COUNT or RELEARN_FLAG_DIAG: the work of the
+                                   search, one per frontier candidate */
     int64_t walk_steps_total;   /* node visits of the grouped root-frontier walks (one node load
                                    per group of source neurons), for the same updates */
     int64_t length_evals_total; /* frontier candidates visited by the mean-length forward and

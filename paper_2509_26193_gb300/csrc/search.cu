@@ -181,6 +181,7 @@ struct SearchArgs {
     int64_t *failed;
     int64_t *evals_total;
     int64_t *steps_total;
+    int count; // add evaluations and walk steps to the totals (RELEARN_FLAG_COUNT or DIAG)
     double *diag_lns;
     int32_t *diag_evals;
     int32_t *diag_restarts;
@@ -221,10 +222,20 @@ __device__ __forceinline__ float attraction(float cnt, float d2, float k2, float
     return __fmul_rn(cnt, ex2_approx(__fmaf_rn(-k2, d2, k2sh)));
 }
 
+// d^2 = dx^2 + dy^2 + dz^2 with (dx, dy) as one packed pair (f32x2 subtract and
+// multiply, sm_100 and later): one instruction fewer than three scalar lanes. Every
+// pass of the search uses this function, so their sums agree bit for bit.
 __device__ __forceinline__ float dist2(float3 x, float4 g)
 {
-    const float dx = __fsub_rn(x.x, g.x), dy = __fsub_rn(x.y, g.y), dz = __fsub_rn(x.z, g.z);
-    return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+    unsigned long long xy, gxy, dxy, sq;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(xy) : "f"(x.x), "f"(x.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(gxy) : "f"(g.x), "f"(g.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dxy) : "l"(xy), "l"(gxy));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(sq) : "l"(dxy));
+    float sx, sy;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(sx), "=f"(sy) : "l"(sq));
+    const float dz = __fsub_rn(x.z, g.z);
+    return __fadd_rn(__fmaf_rn(dz, dz, sx), sy);
 }
 
 // One lane's own walk over [p0, end) starting from running sum cum0: visits
@@ -265,7 +276,9 @@ __device__ __forceinline__ WalkOut walk(const Node *__restrict__ nodes, int32_t 
     return o;
 }
 
-// One step of a 32-lane union walk at node p (see bh_search_kernel).
+// One step of a 32-lane union walk at node p (see bh_search_kernel); kCount: count
+// this lane's evaluations in own.
+template <bool kCount>
 __device__ __forceinline__ void union_step(const Node *__restrict__ nodes, int32_t &p,
                                            int32_t &skip, float &cum, float &comp,
                                            int32_t &own, float3 x, int32_t self_node,
@@ -281,17 +294,19 @@ __device__ __forceinline__ void kahan_add(float &sum, float &c, float a)
     sum = t;
 }
 
+template <bool kCount>
 __device__ __forceinline__ void union_step(const Node *__restrict__ nodes, int32_t &p,
                                            int32_t &skip, float &cum, float &comp,
                                            int32_t &own, float3 x, int32_t self_node,
                                            uint32_t thr0, float k2, float k2sh)
 {
-    const float4 g = __ldg(reinterpret_cast<const float4 *>(&nodes[p].g));
-    const int2 t = __ldg(reinterpret_cast<const int2 *>(&nodes[p].t));
+    float4 g;
+    int2 t;
+    load_node(&nodes[p], g, t);
     const float d2 = dist2(x, g);
     const bool on = p >= skip && g.w > 0.0f;
     const bool pass = __float_as_uint(d2) + (uint32_t)t.y > thr0;
-    own += on ? 1 : 0;
+    if (kCount) own += on ? 1 : 0;
     if (on && pass) {
         skip = t.x;
         if (p != self_node) kahan_add(cum, comp, attraction(g.w, d2, k2, k2sh));
@@ -394,13 +409,18 @@ __device__ __forceinline__ void enqueue_restart(const SearchArgs &a, int32_t k, 
 // nodes and most lanes would idle), or in fixed groups of G = 1, 8, 16 or 32 lanes
 // when search_group forces a width. A warp runs one walk per union, one node load
 // in flight per union and step. Results do not depend on the grouping.
+// 8 blocks of 256 threads per SM (32 registers, the most resident warps): the walk
+// waits on dependent node reads, and more warps hide more of that latency (first
+// update of the clustered benchmark 7.4 ms against 8.1 ms at 6 blocks).
 #ifndef RELEARN_SEARCH_MIN_BLOCKS
-#define RELEARN_SEARCH_MIN_BLOCKS 6 // 40 registers: 6 blocks of 256 threads per SM
+#define RELEARN_SEARCH_MIN_BLOCKS 8
 #endif
 // kBatched: several networks, each source walks its own network's tree (root,
 // subtree end, threshold and kernel width looked up per work item); else one
-// network whose constants are loaded once.
-template <bool kBatched>
+// network whose constants are loaded once. kCount: count evaluations and walk steps
+// (into the context's totals and the per-search diagnostics); counting costs one
+// instruction per union step, so updates that ask for neither skip it.
+template <bool kBatched, bool kCount>
 __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kernel(SearchArgs a)
 {
     const int32_t A = *a.d_A;
@@ -414,7 +434,6 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
         thr0 = __ldg(&a.sc->thr0);
         k2 = __ldg(&a.sc->k2);
     }
-    int64_t my_evals = 0, my_steps = 0;
     int32_t ckp[kMaxCk];
     float ckc[kMaxCk];  // compensated running sum at each checkpoint
     float ckk[kMaxCk];  // its compensation term
@@ -492,7 +511,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
         // ---- pass 1: union of the G root frontiers of this lane's group
         float k2sh = 0.0f;
         double S = 0.0; // the root-level normaliser, FP64
-        int32_t own = 0, nck = 0;
+        int32_t own = 0, nck = 0, task_steps = 0;
         for (int attempt = 0; attempt < 2; ++attempt) {
             int32_t p = root + 1, skip = live ? 0 : 0x7fffffff, steps = 0;
             float cum = 0.0f, comp = 0.0f; // Kahan sum and compensation
@@ -528,14 +547,14 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                         for (; k < kCkStride && p < root_end; k += 4) {
 #pragma unroll
                             for (int u = 0; u < 4; ++u)
-                                union_step(a.nodes, p, skip, cum, comp, own, x, self_node, thr0,
-                                           k2, k2sh);
+                                union_step<kCount>(a.nodes, p, skip, cum, comp, own, x,
+                                                   self_node, thr0, k2, k2sh);
                         }
                     } else {
 #pragma unroll 1
                         for (; k < kCkStride && p < root_end; ++k)
-                            union_step(a.nodes, p, skip, cum, comp, own, x, self_node, thr0, k2,
-                                       k2sh);
+                            union_step<kCount>(a.nodes, p, skip, cum, comp, own, x, self_node,
+                                               thr0, k2, k2sh);
                     }
                     steps += k;
                 }
@@ -554,7 +573,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                     const float d2 = dist2(x, g);
                     const bool on = run && p >= skip && g.w > 0.0f;
                     const bool pass = __float_as_uint(d2) + (uint32_t)t.y > thr0;
-                    own += on ? 1 : 0;
+                    if (kCount) own += on ? 1 : 0;
                     if (on && pass) {
                         skip = t.x;
                         if (p != self_node)
@@ -564,7 +583,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                     if (run) p = down ? p + 1 : max(t.x, p + 1);
                 }
             }
-            if (lane == seg_first) my_steps += steps; // one count per walk
+            if (kCount && lane == seg_first) task_steps += steps; // one count per walk
             nck = ckst & 0xff;
             S = (double)cum - (double)comp;
             // every term underflowed: redo with the exponents shifted by the nearest d^2
@@ -576,62 +595,67 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                 if (w.dmin2 < __int_as_float(0x7f800000)) k2sh = __fmul_rn(k2, w.dmin2);
             }
         }
-        if (!live) continue;
-        my_evals += own;
-
-        // ---- draws: every search of this neuron
-        const int32_t i = a.perm[s];
-        const int32_t nq = max(a.vac_ax[i], 0);
-        const int32_t qbase = a.qoff_o[i];
-        // ln S for the diagnostics only (an FP64 log per source otherwise wasted)
-        const double lns0 = !a.diag_lns ? 0.0
-                            : S > 0.0   ? log(S) - (double)k2sh * 0.6931471805599453
-                                        : -__longlong_as_double(0x7ff0000000000000LL);
-        for (int32_t e = 0; e < nq; ++e) {
-            int32_t result = -1, evals = own, draws = 0;
-            if (S > 0.0) {
-                uint32_t u = philox_x((uint32_t)i, a.step, (uint32_t)e << 8, 0u, a.seed);
-                const double tgt = (double)u * 2.3283064365386963e-10 * S;
-                int lo = 0, hi = nck - 1; // last checkpoint whose sum <= u * S
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if ((double)ckc[mid] - (double)ckk[mid] <= tgt)
-                        lo = mid;
-                    else
-                        hi = mid - 1;
+        int64_t task_evals = own; // 0 on idle lanes (no node is theirs)
+        if (live) {
+            // ---- draws: every search of this neuron
+            const int32_t i = a.perm[s];
+            const int32_t nq = max(a.vac_ax[i], 0);
+            const int32_t qbase = a.qoff_o[i];
+            // ln S for the diagnostics only (an FP64 log per source otherwise wasted)
+            const double lns0 = !a.diag_lns ? 0.0
+                                : S > 0.0   ? log(S) - (double)k2sh * 0.6931471805599453
+                                            : -__longlong_as_double(0x7ff0000000000000LL);
+            for (int32_t e = 0; e < nq; ++e) {
+                int32_t result = -1, evals = own, draws = 0;
+                if (S > 0.0) {
+                    uint32_t u = philox_x((uint32_t)i, a.step, (uint32_t)e << 8, 0u, a.seed);
+                    const double tgt = (double)u * 2.3283064365386963e-10 * S;
+                    int lo = 0, hi = nck - 1; // last checkpoint whose sum <= u * S
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if ((double)ckc[mid] - (double)ckk[mid] <= tgt)
+                            lo = mid;
+                        else
+                            hi = mid - 1;
+                    }
+                    int32_t k = find_root(a.nodes, ckp[lo], root_end, ckc[lo], ckk[lo], x,
+                                          self_node, thr0, k2, k2sh, (float)tgt);
+                    if (k < 0) // u * S rounded up to S past the last weighted candidate
+                        k = find_root(a.nodes, root + 1, root_end, 0.0f, 0.0f, x, self_node,
+                                      thr0, k2, k2sh, __int_as_float(0x7f800000));
+                    if (a.defer && k >= 0 &&
+                        !node_is_leaf((uint32_t)__ldg(&a.nodes[k].t.shift))) {
+                        enqueue_restart(a, k, qbase + e, s, lns0, evals);
+                        continue; // finished by bh_restart_kernel
+                    }
+                    result = restart_chain(a, k, x, self_node, thr0, k2, i, e, evals, draws,
+                                           task_evals);
                 }
-                int32_t k = find_root(a.nodes, ckp[lo], root_end, ckc[lo], ckk[lo], x, self_node,
-                                      thr0, k2, k2sh, (float)tgt);
-                if (k < 0) // u * S rounded up to S past the last weighted candidate
-                    k = find_root(a.nodes, root + 1, root_end, 0.0f, 0.0f, x, self_node, thr0,
-                                  k2, k2sh, __int_as_float(0x7f800000));
-                if (a.defer && k >= 0 &&
-                    !node_is_leaf((uint32_t)__ldg(&a.nodes[k].t.shift))) {
-                    enqueue_restart(a, k, qbase + e, s, lns0, evals);
-                    continue; // finished by bh_restart_kernel
+                const int32_t out = qbase + e;
+                a.req_tgt[out] = result;
+                if (result < 0)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.failed), 1ull);
+                if (a.diag_lns) {
+                    a.diag_lns[out] = lns0;
+                    a.diag_evals[out] = evals;
+                    a.diag_restarts[out] = draws > 0 ? draws - 1 : 0;
                 }
-                result = restart_chain(a, k, x, self_node, thr0, k2, i, e, evals, draws, my_evals);
-            }
-            const int32_t out = qbase + e;
-            a.req_tgt[out] = result;
-            if (result < 0) atomicAdd(reinterpret_cast<unsigned long long *>(a.failed), 1ull);
-            if (a.diag_lns) {
-                a.diag_lns[out] = lns0;
-                a.diag_evals[out] = evals;
-                a.diag_restarts[out] = draws > 0 ? draws - 1 : 0;
             }
         }
+        if constexpr (kCount) { // this task's counts: one atomic per warp
+            int64_t ts = task_steps;
+            for (int off = 16; off; off >>= 1) {
+                task_evals += __shfl_xor_sync(0xffffffffu, task_evals, off);
+                ts += __shfl_xor_sync(0xffffffffu, ts, off);
+            }
+            if (lane == 0 && task_evals)
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.evals_total),
+                          (unsigned long long)task_evals);
+            if (lane == 0 && ts)
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.steps_total),
+                          (unsigned long long)ts);
+        }
     }
-    for (int off = 16; off; off >>= 1) {
-        my_evals += __shfl_xor_sync(0xffffffffu, my_evals, off);
-        my_steps += __shfl_xor_sync(0xffffffffu, my_steps, off);
-    }
-    if (lane == 0 && my_evals)
-        atomicAdd(reinterpret_cast<unsigned long long *>(a.evals_total),
-                  (unsigned long long)my_evals);
-    if (lane == 0 && my_steps)
-        atomicAdd(reinterpret_cast<unsigned long long *>(a.steps_total),
-                  (unsigned long long)my_steps);
 }
 
 // ---------------------------------------------------------------------------
@@ -932,10 +956,10 @@ __global__ void __launch_bounds__(256) bh_split_kernel(SearchArgs a)
         my_evals += __shfl_xor_sync(0xffffffffu, my_evals, off);
         my_steps += __shfl_xor_sync(0xffffffffu, my_steps, off);
     }
-    if (lane == 0 && my_evals)
+    if (a.count && lane == 0 && my_evals)
         atomicAdd(reinterpret_cast<unsigned long long *>(a.evals_total),
                   (unsigned long long)my_evals);
-    if (lane == 0 && my_steps)
+    if (a.count && lane == 0 && my_steps)
         atomicAdd(reinterpret_cast<unsigned long long *>(a.steps_total),
                   (unsigned long long)my_steps);
 }
@@ -978,7 +1002,7 @@ __global__ void __launch_bounds__(256) bh_restart_kernel(SearchArgs a, const uin
         }
     }
     for (int off = 16; off; off >>= 1) my_evals += __shfl_xor_sync(0xffffffffu, my_evals, off);
-    if ((threadIdx.x & 31) == 0 && my_evals)
+    if (a.count && (threadIdx.x & 31) == 0 && my_evals)
         atomicAdd(reinterpret_cast<unsigned long long *>(a.evals_total),
                   (unsigned long long)my_evals);
 }
@@ -1045,6 +1069,7 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     a.evals_total = c->d_i64 + I64_EVALS_TOTAL;
     a.steps_total = c->d_i64 + I64_STEPS_TOTAL;
     const bool diag = (p.flags & RELEARN_FLAG_DIAG) != 0;
+    a.count = diag || (p.flags & RELEARN_FLAG_COUNT) != 0;
     a.diag_lns = diag ? c->d_diag_lns : nullptr;
     a.diag_evals = diag ? c->d_diag_evals : nullptr;
     a.diag_restarts = diag ? c->d_diag_restarts : nullptr;
@@ -1066,13 +1091,20 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     const bool depths = sg >= 1000 && sg < 3000;
     a.spread_depth = depths ? (int)((sg - 1000) / 100) : -1;
     a.n_total = c->n;
-    void (*kern)(SearchArgs) = a.net ? bh_search_kernel<true> : bh_search_kernel<false>;
+    void (*kern)(SearchArgs) = a.net ? (a.count ? bh_search_kernel<true, true>
+                                                : bh_search_kernel<true, false>)
+                                     : (a.count ? bh_search_kernel<false, true>
+                                                : bh_search_kernel<false, false>);
     void (*split)(SearchArgs) = a.net ? bh_split_kernel<true> : bh_split_kernel<false>;
     // resident blocks per SM of both kernels, queried once per context and kernel pair
     int *occ = c->search_occ[a.net ? 1 : 0];
     if (occ[0] == 0) {
         int per_sm = 0, per_sm_split = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0))) return e;
+        // both counting variants have the same launch bounds
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                 &per_sm, a.net ? bh_search_kernel<true, false> : bh_search_kernel<false, false>,
+                 256, 0)))
+            return e;
         if ((e = cudaFuncSetAttribute(split, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kSplitSmem)))
             return e;

@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CAPACITY", 5
 FLAG_DIAG = 1
 FLAG_TIMING = 2
 FLAG_REGROUP = 4
+FLAG_COUNT = 8
 
 _lock = threading.Lock()
 _lib = None
