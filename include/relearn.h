@@ -227,14 +227,14 @@ relearn_status relearn_update_connectivity_typed(relearn_ctx *ctx, const relearn
                                                  int32_t *vac_de_inh, const uint8_t *type,
                                                  relearn_update_stats *stats, void *stream);
 
-/* Testing hook for the bounded waits of the bottom-up update (its single-pass prefix,
- * where each tile of 1024 Morton positions waits for the sums its predecessors
- * publish): in the next update, or mean-length call, of this context the prefix tile
- * `tile` publishes nothing, so the tiles after it wait until their bound runs out
- * (2^16 rounds of reads, tens of milliseconds). That call then reports
- * RELEARN_ERR_TIMEOUT at its next synchronising call and the update applies nothing;
- * the context stays usable. tile < 0 clears the hook. Errors: INVALID_ARG for NULL. */
-relearn_status relearn_debug_stall_reduce(relearn_ctx *ctx, int64_t tile);
+/* Testing hook for the bounded waits of the update's query setup (a single-pass scan
+ * in which each tile of 4096 neurons waits for the sums its predecessors publish): in
+ * the next update of this context the scan tile `tile` publishes nothing, so the tiles
+ * after it wait until their bound runs out (2^16 rounds of reads, tens of
+ * milliseconds). That update then reports RELEARN_ERR_TIMEOUT at its next
+ * synchronising call and applies nothing; the context stays usable. tile < 0 clears
+ * the hook. Errors: INVALID_ARG for NULL. */
+relearn_status relearn_debug_stall_scan(relearn_ctx *ctx, int64_t tile);
 
 /* Deletion pass (Sec. III-A "Update of synapses", first sub-phase).
  *   retract_ax, retract_de  device int32[n] (>= 0): elements each neuron retracts.

@@ -79,7 +79,7 @@ void free_all(relearn_ctx *c)
         (void **)&c->d_codes_alt, (void **)&c->d_perm,      (void **)&c->d_perm_alt,
         (void **)&c->d_pos,      (void **)&c->d_posq,       (void **)&c->d_mask,       (void **)&c->d_base,
         (void **)&c->d_nodes,    (void **)&c->d_parent,     (void **)&c->d_nsize,
-        (void **)&c->d_leaf,     (void **)&c->d_acc,        (void **)&c->d_lb,
+        (void **)&c->d_leaf,     (void **)&c->d_acc,
         (void **)&c->d_cnt,      (void **)&c->d_act_off,    (void **)&c->d_qoff_o,
         (void **)&c->d_act_src,  (void **)&c->d_req_src,    (void **)&c->d_req_elem,
         (void **)&c->d_req_tgt,  (void **)&c->d_req_acc,    (void **)&c->d_req_prio,
@@ -222,8 +222,7 @@ relearn_status relearn_create_batched(relearn_ctx **out, int device, int64_t max
     A(d_parent, M);
     A(d_nsize, M);
     A(d_leaf, N);
-    A(d_acc, 4 * M + 8 * (N / 1024 + 2)); // L4 prefix (n + 1) and 2 per prefix tile
-    A(d_lb, N / 1024 + 3);
+    A(d_acc, 4 * M + 8 * (N / 1024 + 2)); // L4 prefix (n + 1) and the prefix tiles' sums
     A(d_cnt, N + 1);
     A(d_act_off, N + 1);
     A(d_qoff_o, N + 1);
@@ -270,7 +269,7 @@ relearn_status relearn_create_batched(relearn_ctx **out, int device, int64_t max
     A(sort.hist, 256 * sort_blocks);
     int64_t scan_blocks = std::max({scan_blocks_needed(N + 1), scan_blocks_needed(QC),
                                     scan_blocks_needed(S), scan_blocks_needed(256 * sort_blocks)});
-    A(scan.block_sums, 2 * scan_blocks);
+    A(scan.block_sums, 4 * scan_blocks); // a pair scan keeps two sums per tile
     A(scan.flags, scan_blocks + 3);
 #undef A
     if (e == cudaSuccess) {
@@ -478,7 +477,7 @@ relearn_status relearn_update_connectivity_typed(relearn_ctx *c, const relearn_p
     return RELEARN_OK;
 }
 
-relearn_status relearn_debug_stall_reduce(relearn_ctx *c, int64_t tile)
+relearn_status relearn_debug_stall_scan(relearn_ctx *c, int64_t tile)
 {
     if (!c) return RELEARN_ERR_INVALID_ARG;
     c->debug_stall_tile = tile < 0 ? -1 : tile;

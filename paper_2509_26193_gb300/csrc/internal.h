@@ -11,7 +11,8 @@ namespace rl {
 
 // Scratch of the device-wide single-pass exclusive scan.
 struct ScanScratch {
-    int64_t *block_sums = nullptr; // [2 * max_blocks]: tile sums, then inclusive prefixes
+    int64_t *block_sums = nullptr; // [4 * max_blocks]: tile sums, then inclusive prefixes
+                                   // (pairs of them for a pair scan)
     int32_t *flags = nullptr;      // [max_blocks + 3]: ticket, abort, blocks done, tile
                                    // states; zero between scans
     int32_t *status = nullptr;     // device status word for a wait that ran out (or NULL)
@@ -87,8 +88,7 @@ struct relearn_ctx {
     int32_t *d_nsize = nullptr;                          // [max_nodes] neurons in the node's cell
     int32_t *d_leaf = nullptr;                           // [n] leaf node of each position
     double *d_acc = nullptr;  // bottom-up update: int64 x 4 prefix and tile sums
-    int32_t *d_lb = nullptr;  // [max_neurons / 1024 + 3] single-pass prefix tile states
-    int64_t debug_stall_tile = -1; // relearn_debug_stall_reduce: next update only
+    int64_t debug_stall_tile = -1; // relearn_debug_stall_scan: next update only
 
     // ---- queries and requests (per update)
     int32_t *d_cnt = nullptr;       // [n + 1] scratch counts

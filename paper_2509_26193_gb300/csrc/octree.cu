@@ -456,10 +456,12 @@ __device__ __forceinline__ L4 l4_shfl_up(L4 v, int o)
               __shfl_up_sync(0xffffffffu, v.y, o), __shfl_up_sync(0xffffffffu, v.z, o)};
 }
 
-// Inclusive block scan of L4 (256 threads); *total = block sum.
+// Inclusive block scan of L4 over NT threads; *total = block sum.
+template <int NT = 256>
 __device__ __forceinline__ L4 l4_block_inclusive(L4 v, L4 *total)
 {
-    __shared__ L4 wt[8];
+    constexpr int NW = NT / 32;
+    __shared__ L4 wt[NW];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -469,17 +471,17 @@ __device__ __forceinline__ L4 l4_block_inclusive(L4 v, L4 *total)
     if (lane == 31) wt[warp] = v;
     __syncthreads();
     if (warp == 0) {
-        L4 w = lane < 8 ? wt[lane] : L4{0, 0, 0, 0};
+        L4 w = lane < NW ? wt[lane] : L4{0, 0, 0, 0};
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
+        for (int o = 1; o < NW; o <<= 1) {
             L4 t = l4_shfl_up(w, o);
             if (lane >= o) w = l4_add(w, t);
         }
-        if (lane < 8) wt[lane] = w;
+        if (lane < NW) wt[lane] = w;
     }
     __syncthreads();
     if (warp > 0) v = l4_add(v, wt[warp - 1]);
-    *total = wt[7];
+    *total = wt[NW - 1];
     __syncthreads();
     return v;
 }
@@ -487,156 +489,151 @@ __device__ __forceinline__ L4 l4_block_inclusive(L4 v, L4 *total)
 constexpr int kRedItems = 4;
 constexpr int kRedTile = 256 * kRedItems;
 
-// Leaf geometry (optionally written) plus w of Morton position s.
-__device__ __forceinline__ L4 leaf_weight(Node *nodes, const int32_t *leaf_of,
-                                          const int32_t *perm, const float4 *pos,
-                                          const int4 *posq, const int32_t *vac_de, int64_t s,
-                                          bool write_leaf)
-{
-    int32_t c = vac_de[perm[s]];
-    if (c < 0) c = 0;
-    if (write_leaf) {
-        const float4 p = pos[s];
-        const int32_t v = leaf_of[s];
-        nodes[v].g = c > 0 ? NodeGeo{p.x, p.y, p.z, (float)c} : NodeGeo{0.f, 0.f, 0.f, 0.f};
-        nodes[v].t.icount = c;
-    }
-    const int4 q = posq[s];
-    const long long lc = c;
-    return L4{lc, lc * q.x, lc * q.y, lc * q.z};
-}
+// The prefix P runs in three passes with no waiting between blocks: leaves and tile
+// sums, a scan of the tile sums in one block, then each tile's prefix.
 
-// Single pass over the leaves (decoupled look-back): each block takes the next
-// tile by ticket, writes the tile's leaves and sums their weights, publishes the
-// tile sum, then its first warp reads the states of the 32 preceding tiles at
-// once and adds their published sums back to the nearest one that has published
-// its inclusive prefix (further windows of 32 if none has), and the block
-// publishes its own inclusive prefix. A block only waits for tiles with smaller
-// tickets, which are already running or done and publish their sums before they
-// wait themselves, so every wait ends; each is still bounded (kLbSpin rounds,
-// then RELEARN_ERR_TIMEOUT in *status and no block waits any more).
-// lb[0]: ticket counter, lb[1]: abort flag, lb[2 + t]: state of tile t; all zero
-// at launch.
-constexpr int32_t kLbAgg = 1, kLbInc = 2;
-constexpr int kLbSpin = 1 << 16;
-
-__device__ __forceinline__ L4 l4_load_volatile(const L4 *p)
+// Sum of v over a block of 256 threads (every thread receives it).
+__device__ __forceinline__ L4 l4_block_sum(L4 v, L4 *wt)
 {
-    const volatile long long *q = reinterpret_cast<const volatile long long *>(p);
-    return L4{q[0], q[1], q[2], q[3]};
-}
-
-__device__ __forceinline__ L4 l4_warp_sum(L4 v)
-{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o; o >>= 1)
         v = l4_add(v, L4{__shfl_xor_sync(0xffffffffu, v.c, o), __shfl_xor_sync(0xffffffffu, v.x, o),
-                         __shfl_xor_sync(0xffffffffu, v.y, o), __shfl_xor_sync(0xffffffffu, v.z, o)});
-    return v;
+                         __shfl_xor_sync(0xffffffffu, v.y, o),
+                         __shfl_xor_sync(0xffffffffu, v.z, o)});
+    if (lane == 0) wt[warp] = v;
+    __syncthreads();
+    L4 t{0, 0, 0, 0};
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t = l4_add(t, wt[w]);
+    __syncthreads();
+    return t;
 }
 
+// Pass 1: the leaf nodes of tile t (whole 32-byte nodes; consecutive threads on
+// consecutive Morton positions) and the tile's sum of w.
 __global__ void __launch_bounds__(256)
-    reduce_scan_kernel(Node *nodes, const int32_t *__restrict__ leaf_of,
-                       const int32_t *__restrict__ perm, const float4 *__restrict__ pos,
-                       const int4 *__restrict__ posq, const int32_t *__restrict__ vac_de,
-                       int64_t n, int64_t nb, int32_t *lb, L4 *agg, L4 *inc,
-                       L4 *__restrict__ P, int32_t *status, int64_t stall_tile)
+    reduce_leaves_kernel(Node *__restrict__ nodes, const int32_t *__restrict__ leaf_of,
+                         const int32_t *__restrict__ perm, const float4 *__restrict__ pos,
+                         const int4 *__restrict__ posq, const int32_t *__restrict__ vac_de,
+                         int64_t n, L4 *__restrict__ tile_sum)
 {
-    __shared__ int32_t s_tile;
-    __shared__ L4 s_prefix;
-    if (threadIdx.x == 0) s_tile = atomicAdd(&lb[0], 1);
-    __syncthreads();
-    const int64_t t = s_tile;
-    const int64_t base = t * kRedTile + (int64_t)threadIdx.x * kRedItems;
+    __shared__ L4 s_part[8];
+    const int64_t tile0 = (int64_t)blockIdx.x * kRedTile;
+    L4 acc{0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < kRedItems; ++k) {
+        const int64_t s = tile0 + k * 256 + threadIdx.x;
+        if (s < n) {
+            int32_t c = vac_de[perm[s]];
+            if (c < 0) c = 0;
+            const float4 p = pos[s];
+            const int32_t v = leaf_of[s];
+            Node nd;
+            nd.g = c > 0 ? NodeGeo{p.x, p.y, p.z, (float)c} : NodeGeo{0.f, 0.f, 0.f, 0.f};
+            nd.t = NodeTopo{v + 1, kLeafShift, (int32_t)s, c};
+            nodes[v] = nd;
+            const int4 q = posq[s];
+            const long long lc = c;
+            acc = l4_add(acc, L4{lc, lc * q.x, lc * q.y, lc * q.z});
+        }
+    }
+    const L4 tot = l4_block_sum(acc, s_part);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+// Pass 2 (one block of 1024 threads): tile sums -> exclusive tile prefixes, in place;
+// P[n] = the total.
+__global__ void __launch_bounds__(1024)
+    reduce_tiles_kernel(L4 *__restrict__ tile_sum, int64_t nb, L4 *__restrict__ P, int64_t n)
+{
+    const int64_t per = (nb + 1023) / 1024;
+    const int64_t j0 = min((int64_t)threadIdx.x * per, nb), j1 = min(j0 + per, nb);
+    L4 acc{0, 0, 0, 0};
+    for (int64_t j = j0; j < j1; ++j) acc = l4_add(acc, tile_sum[j]);
+    L4 tot;
+    L4 run = l4_sub(l4_block_inclusive<1024>(acc, &tot), acc);
+    for (int64_t j = j0; j < j1; ++j) {
+        const L4 w = tile_sum[j];
+        tile_sum[j] = run;
+        run = l4_add(run, w);
+    }
+    if (threadIdx.x == 0) P[n] = tot;
+}
+
+// Pass 3: P over tile t = the tile's prefix + the exclusive scan of w inside the tile
+// (thread i: positions 4i .. 4i + 3 of the tile).
+__global__ void __launch_bounds__(256)
+    reduce_prefix_kernel(const int32_t *__restrict__ perm, const int4 *__restrict__ posq,
+                         const int32_t *__restrict__ vac_de, int64_t n,
+                         const L4 *__restrict__ tile_pre, L4 *__restrict__ P)
+{
+    const int64_t s0 = (int64_t)blockIdx.x * kRedTile + (int64_t)threadIdx.x * kRedItems;
     L4 w[kRedItems];
     L4 acc{0, 0, 0, 0};
+#pragma unroll
     for (int k = 0; k < kRedItems; ++k) {
-        w[k] = base + k < n ? leaf_weight(nodes, leaf_of, perm, pos, posq, vac_de, base + k, true)
-                            : L4{0, 0, 0, 0};
+        const int64_t s = s0 + k;
+        w[k] = L4{0, 0, 0, 0};
+        if (s < n) {
+            int32_t c = vac_de[perm[s]];
+            if (c < 0) c = 0;
+            const int4 q = posq[s];
+            const long long lc = c;
+            w[k] = L4{lc, lc * q.x, lc * q.y, lc * q.z};
+        }
         acc = l4_add(acc, w[k]);
     }
     L4 tot;
-    const L4 incl = l4_block_inclusive(acc, &tot);
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        volatile int32_t *state = lb + 2;
-        L4 prefix{0, 0, 0, 0};
-        // stall_tile (a test of the bounded waits): that tile never publishes
-        const bool publish = t != stall_tile;
-        if (t > 0) {
-            if (lane == 0 && publish) {
-                agg[t] = tot;
-                __threadfence();
-                atomicExch(&lb[2 + t], kLbAgg);
-            }
-            for (int64_t j0 = t - 1;; j0 -= 32) {
-                const int64_t j = j0 - lane; // this lane's predecessor (j < 0: prefix zero)
-                int32_t f = j < 0 ? kLbInc : 0;
-                bool ready = false;
-                for (int spin = 0; spin < kLbSpin; ++spin) {
-                    if (j >= 0) f = state[j];
-                    ready = __all_sync(0xffffffffu, f != 0);
-                    if (ready || *(volatile int32_t *)&lb[1]) break;
-                }
-                if (!ready) { // gave up (or another block did): report, stop waiting
-                    if (lane == 0) {
-                        set_status(status, RELEARN_ERR_TIMEOUT);
-                        atomicExch(&lb[1], 1);
-                    }
-                    break;
-                }
-                __threadfence();
-                const uint32_t incm = __ballot_sync(0xffffffffu, f == kLbInc);
-                const int stop = incm ? __ffs(incm) - 1 : 32; // nearest inclusive prefix
-                L4 v{0, 0, 0, 0};
-                if (j >= 0 && lane < stop) v = l4_load_volatile(&agg[j]);
-                if (j >= 0 && lane == stop) v = l4_load_volatile(&inc[j]);
-                prefix = l4_add(prefix, l4_warp_sum(v));
-                if (incm) break;
-            }
-        }
-        if (lane == 0) {
-            if (publish) {
-                inc[t] = l4_add(prefix, tot);
-                __threadfence();
-                atomicExch(&lb[2 + t], kLbInc);
-            }
-            s_prefix = prefix;
-            if (t == nb - 1) P[n] = l4_add(prefix, tot);
-        }
-    }
-    __syncthreads();
-    L4 run = l4_add(s_prefix, l4_sub(incl, acc));
+    L4 run = l4_add(tile_pre[blockIdx.x], l4_sub(l4_block_inclusive(acc, &tot), acc));
+#pragma unroll
     for (int k = 0; k < kRedItems; ++k) {
-        if (base + k < n) P[base + k] = run;
+        if (s0 + k < n) P[s0 + k] = run;
         run = l4_add(run, w[k]);
     }
 }
 
-// Inner nodes: exact sums from the prefix, centroid rounded once to FP32.
+__device__ __forceinline__ void inner_sums(Node *__restrict__ nodes, int64_t v, int64_t first,
+                                           int64_t size, const L4 *__restrict__ P,
+                                           const Geom *g)
+{
+    const double ox = g->fx_lo[0], oy = g->fx_lo[1], oz = g->fx_lo[2], inv = g->fx_inv;
+    const L4 s = l4_sub(P[first + size], P[first]);
+    if (s.c > 0) {
+        const double r = inv / (double)s.c;
+        nodes[v].g = NodeGeo{__double2float_rn(ox + (double)s.x * r),
+                             __double2float_rn(oy + (double)s.y * r),
+                             __double2float_rn(oz + (double)s.z * r), (float)s.c};
+    } else {
+        nodes[v].g = NodeGeo{0.f, 0.f, 0.f, 0.f};
+    }
+    nodes[v].t.icount = (int32_t)s.c;
+}
+
+// Inner nodes: exact sums from the prefix, centroid rounded once to FP32. Every inner
+// node but a network root holds at least two neurons, so nodes with nsize < 2 (the
+// leaves, written by reduce_leaves_kernel) are passed over without reading them;
+// thread b < B handles network b's root if it sits above a single leaf.
 __global__ void reduce_nodes_kernel(Node *__restrict__ nodes, const int32_t *__restrict__ nsize,
                                     const int64_t *d_num_nodes, const L4 *__restrict__ P,
                                     const int32_t *__restrict__ net,
-                                    const Geom *__restrict__ g_all)
+                                    const Geom *__restrict__ g_all,
+                                    const int32_t *__restrict__ root,
+                                    const int64_t *__restrict__ off, int32_t B, int64_t n)
 {
     const int64_t m = *d_num_nodes;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < m;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const int2 t = *reinterpret_cast<const int2 *>(&nodes[v].t);
-        if (node_is_leaf((uint32_t)t.y)) continue;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid < B) {
+        const int32_t v = B > 1 ? root[tid] : 0;
+        const int64_t first = B > 1 ? off[tid] : 0, last = B > 1 ? off[tid + 1] : n;
+        if (last - first < 2 && !node_is_leaf(nodes[v].t.shift)) // a root above one leaf
+            inner_sums(nodes, v, first, last - first, P, g_all + tid);
+    }
+    for (int64_t v = tid; v < m; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t size = nsize[v];
+        if (size < 2) continue;
         const int32_t first = nodes[v].t.neuron;
-        const Geom *g = g_all + net_at(net, first);
-        const double ox = g->fx_lo[0], oy = g->fx_lo[1], oz = g->fx_lo[2], inv = g->fx_inv;
-        const L4 s = l4_sub(P[first + nsize[v]], P[first]);
-        if (s.c > 0) {
-            const double r = inv / (double)s.c;
-            nodes[v].g = NodeGeo{__double2float_rn(ox + (double)s.x * r),
-                                 __double2float_rn(oy + (double)s.y * r),
-                                 __double2float_rn(oz + (double)s.z * r), (float)s.c};
-        } else {
-            nodes[v].g = NodeGeo{0.f, 0.f, 0.f, 0.f};
-        }
-        nodes[v].t.icount = (int32_t)s.c;
+        inner_sums(nodes, v, first, size, P, g_all + net_at(net, first));
     }
 }
 
@@ -724,19 +721,22 @@ cudaError_t octree_reduce(relearn_ctx *c, const int32_t *vac_de, cudaStream_t st
     const int64_t n = c->n;
     const int64_t nb = (n + kRedTile - 1) / kRedTile;
     L4 *P = reinterpret_cast<L4 *>(c->d_acc); // n + 1 prefix entries
-    L4 *agg = P + (n + 1);                      // nb tile sums, nb inclusive prefixes
-    L4 *inc = agg + nb;
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(c->d_lb, 0, (size_t)(nb + 2) * sizeof(int32_t), st))) return e;
-    reduce_scan_kernel<<<(unsigned)nb, 256, 0, st>>>(c->d_nodes, c->d_leaf, c->d_perm, c->d_pos,
-                                                      c->d_posq, vac_de, n, nb, c->d_lb, agg,
-                                                      inc, P, c->d_status,
-                                                      c->debug_stall_tile);
-    c->debug_stall_tile = -1; // one update only
+    L4 *tile = P + (n + 1);                     // nb tile sums, then tile prefixes
+    if (nb > 0) {
+        reduce_leaves_kernel<<<(unsigned)nb, 256, 0, st>>>(c->d_nodes, c->d_leaf, c->d_perm,
+                                                            c->d_pos, c->d_posq, vac_de, n, tile);
+        note_launch();
+    }
+    reduce_tiles_kernel<<<1, 1024, 0, st>>>(tile, nb, P, n);
     note_launch();
+    if (nb > 0) {
+        reduce_prefix_kernel<<<(unsigned)nb, 256, 0, st>>>(c->d_perm, c->d_posq, vac_de, n, tile,
+                                                            P);
+        note_launch();
+    }
     reduce_nodes_kernel<<<grid_for(c->max_nodes, 256, c->num_sms), 256, 0, st>>>(
         c->d_nodes, c->d_nsize, c->d_i64 + I64_NODES, P, c->num_nets > 1 ? c->d_net : nullptr,
-        c->d_geom);
+        c->d_geom, c->d_root, c->d_off, c->num_nets, n);
     note_launch();
     return cudaGetLastError();
 }

@@ -39,6 +39,7 @@
 #include <cooperative_groups.h>
 
 #include "internal.h"
+#include "scan_pair.cuh"
 
 namespace rl {
 
@@ -98,70 +99,74 @@ __global__ void search_const_kernel(const Geom *g_all, int32_t B, float sigma, f
     if (b < B) search_const_one(b, g_all, sigma, theta, net_sigma, net_theta, sc_all, status);
 }
 
-// active[s] = 1 if the neuron at Morton position s has vacant axonal elements;
-// cnt_id[i] = its number of searches (canonical request order is by id). Thread b < B
-// also forms network b's search constants (as search_const_kernel; the grid covers B
-// since every network holds a neuron).
-__global__ void query_counts_kernel(const int32_t *__restrict__ vac_ax,
-                                    const int32_t *__restrict__ perm, int64_t n,
-                                    int32_t *__restrict__ active, int32_t *__restrict__ cnt_id,
-                                    const Geom *g_all, int32_t B, float sigma, float theta,
-                                    const float *net_sigma, const float *net_theta,
-                                    SearchConst *sc_all, int32_t *status)
-{
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid < B)
-        search_const_one((int32_t)tid, g_all, sigma, theta, net_sigma, net_theta, sc_all,
-                         status);
-    for (int64_t s = tid; s <= n;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        if (s == n) {
-            active[n] = 0;
-            cnt_id[n] = 0;
-            continue;
-        }
-        active[s] = vac_ax[perm[s]] > 0 ? 1 : 0;
-        int32_t b = vac_ax[s];
-        cnt_id[s] = b > 0 ? b : 0;
-    }
-}
+// The query setup of an update in one pass (a pair scan, scan_pair.cuh): over index
+// k < n, a = 1 if the neuron at Morton position k has vacant axonal elements, b = the
+// number of searches of neuron id k (canonical request order is by id). Their
+// exclusive prefixes place the sources (act_src, Morton order) and the request records
+// (id order, qoff_o); thread i < B of the grid also forms network i's search
+// constants. Q = total searches; beyond capacity the update is void (status
+// CAPACITY), and so it is while an earlier device error (e.g. a bad per-network
+// parameter) is unread: finish() publishes Q and the source count only then.
+struct QueryOp {
+    const int32_t *__restrict__ vac_ax;
+    const int32_t *__restrict__ perm;
+    int64_t n, max_searches;
+    int32_t *__restrict__ qoff_o;
+    int32_t *__restrict__ act_src;
+    int32_t *__restrict__ req_src;
+    int32_t *__restrict__ req_elem;
+    int32_t *__restrict__ req_tgt;
+    int64_t *d_total, *d_active; // totals of the pass
+    int32_t *d_Q, *d_A;          // what the search and the acceptance read
+    int64_t *d_Qout, *d_Qsum;    // Q of this update, searches of every update
+    int32_t *status;
+    // search constants
+    const Geom *g_all;
+    int32_t B;
+    float sigma, theta;
+    const float *net_sigma, *net_theta;
+    SearchConst *sc_all;
 
-// Q = total searches; beyond capacity the update is void (status CAPACITY), and so it
-// is while an earlier device error (e.g. a bad per-network parameter) is unread. Every
-// block forms the same Q from the same totals; block 0 publishes it. Then the source
-// list (Morton order) and the request records (id order) are filled.
-__global__ void query_fill_kernel(const int32_t *__restrict__ vac_ax, int64_t n,
-                                  const int32_t *__restrict__ active,
-                                  const int32_t *__restrict__ act_off,
-                                  const int32_t *__restrict__ qoff_o, const int64_t *d_total,
-                                  const int64_t *d_active, int64_t max_searches, int32_t *d_Q,
-                                  int32_t *d_A, int64_t *d_Qout, int64_t *d_Qsum, int32_t *status,
-                                  int32_t *__restrict__ act_src, int32_t *__restrict__ req_src,
-                                  int32_t *__restrict__ req_elem, int32_t *__restrict__ req_tgt)
-{
-    const int64_t q = *d_total;
-    const bool over = q > max_searches;
-    const bool void_ = over || *(volatile int32_t *)status != 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *d_Qout = q;
+    __device__ void prologue(int64_t i, int64_t stride) const
+    {
+        for (int64_t b = i; b < B; b += stride)
+            search_const_one((int32_t)b, g_all, sigma, theta, net_sigma, net_theta, sc_all,
+                             status);
+    }
+    __device__ int2 load(int64_t k) const
+    {
+        const int32_t c = vac_ax[k];
+        return make_int2(vac_ax[perm[k]] > 0 ? 1 : 0, c > 0 ? c : 0);
+    }
+    __device__ void emit(int64_t k, int64_t a, int64_t q, int2 v) const
+    {
+        qoff_o[k] = (int32_t)q;
+        if (v.x) act_src[a] = (int32_t)k;
+        // requests past the capacity are not written (the update is then void)
+        for (int32_t e = 0; e < v.y && q + e < max_searches; ++e) {
+            req_src[q + e] = (int32_t)k;
+            req_elem[q + e] = e;
+            req_tgt[q + e] = -1;
+        }
+    }
+    __device__ void store_totals(int64_t a, int64_t q) const
+    {
+        *d_active = a;
+        *d_total = q;
+        qoff_o[n] = (int32_t)q;
+    }
+    __device__ void finish() const
+    {
+        const int64_t q = *(volatile int64_t *)d_total;
+        const bool over = q > max_searches;
         if (over) set_status(status, RELEARN_ERR_CAPACITY);
+        const bool void_ = over || *(volatile int32_t *)status != 0;
+        *d_Qout = q;
         *d_Q = void_ ? 0 : (int32_t)q;
-        *d_A = void_ ? 0 : (int32_t)*d_active;
+        *d_A = void_ ? 0 : (int32_t)*(volatile int64_t *)d_active;
         *d_Qsum += void_ ? 0 : q;
     }
-    if (void_) return;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        if (active[s]) act_src[act_off[s]] = (int32_t)s;
-        int32_t c = vac_ax[s];
-        int32_t b1 = qoff_o[s];
-        for (int32_t e = 0; e < c; ++e) {
-            req_src[b1 + e] = (int32_t)s;
-            req_elem[b1 + e] = e;
-            req_tgt[b1 + e] = -1;
-        }
-    }
-}
+};
 
 struct SearchArgs {
     const Node *__restrict__ nodes;
@@ -1021,25 +1026,37 @@ cudaError_t search_constants(relearn_ctx *c, const relearn_params &p, cudaStream
 cudaError_t search_prepare(relearn_ctx *c, const relearn_params &p, const int32_t *vac_ax,
                            cudaStream_t st)
 {
-    cudaError_t e;
     const int64_t n = c->n;
-    int32_t *active = c->d_cnt, *cnt_o = c->d_tcnt; // scratch
-    // grid_for(n + 1) threads cover every network: each holds at least one neuron
-    query_counts_kernel<<<grid_for(n + 1, 256, c->num_sms), 256, 0, st>>>(
-        vac_ax, c->d_perm, n, active, cnt_o, c->d_geom, c->num_nets, p.sigma, p.theta,
-        p.net_sigma, p.net_theta, c->d_sc, c->d_status);
-    note_launch();
-    if ((e = scan_exclusive(active, c->d_act_off, n + 1, nullptr, c->d_i64 + I64_ACTIVE, c->scan,
-                            st)))
-        return e;
-    if ((e = scan_exclusive(cnt_o, c->d_qoff_o, n + 1, nullptr, c->d_i64 + I64_SCAN_TOTAL,
-                            c->scan, st)))
-        return e;
-    query_fill_kernel<<<grid_for(n, 256, c->num_sms), 256, 0, st>>>(
-        vac_ax, n, active, c->d_act_off, c->d_qoff_o, c->d_i64 + I64_SCAN_TOTAL,
-        c->d_i64 + I64_ACTIVE, c->max_searches, c->d_i32 + I32_Q, c->d_i32 + I32_ACTIVE,
-        c->d_i64 + I64_Q, c->d_i64 + I64_Q_TOTAL, c->d_status, c->d_act_src, c->d_req_src,
-        c->d_req_elem, c->d_req_tgt);
+    QueryOp op;
+    op.vac_ax = vac_ax;
+    op.perm = c->d_perm;
+    op.n = n;
+    op.max_searches = c->max_searches;
+    op.qoff_o = c->d_qoff_o;
+    op.act_src = c->d_act_src;
+    op.req_src = c->d_req_src;
+    op.req_elem = c->d_req_elem;
+    op.req_tgt = c->d_req_tgt;
+    op.d_total = c->d_i64 + I64_SCAN_TOTAL;
+    op.d_active = c->d_i64 + I64_ACTIVE;
+    op.d_Q = c->d_i32 + I32_Q;
+    op.d_A = c->d_i32 + I32_ACTIVE;
+    op.d_Qout = c->d_i64 + I64_Q;
+    op.d_Qsum = c->d_i64 + I64_Q_TOTAL;
+    op.status = c->d_status;
+    op.g_all = c->d_geom;
+    op.B = c->num_nets;
+    op.sigma = p.sigma;
+    op.theta = p.theta;
+    op.net_sigma = p.net_sigma;
+    op.net_theta = p.net_theta;
+    op.sc_all = c->d_sc;
+    const int64_t tiles = std::max<int64_t>(1, (n + pair_scan::kTile - 1) / pair_scan::kTile);
+    if (tiles > c->scan.max_blocks) return cudaErrorInvalidValue;
+    pair_scan::scan_pair_kernel<QueryOp><<<(unsigned)tiles, pair_scan::kThreads, 0, st>>>(
+        op, n, c->scan.flags, reinterpret_cast<longlong2 *>(c->scan.block_sums), c->d_status,
+        c->debug_stall_tile);
+    c->debug_stall_tile = -1; // one update only
     note_launch();
     return cudaGetLastError();
 }

@@ -73,7 +73,7 @@ _SIGS = {
                                 ctypes.POINTER(_I64), _P],
     "relearn_deliver_spikes": [_P, _P, _P, _P],
     "relearn_mean_length": [_P, ctypes.POINTER(relearn_params), _P, _P, _P, _P, _P],
-    "relearn_debug_stall_reduce": [_P, ctypes.c_int64],
+    "relearn_debug_stall_scan": [_P, ctypes.c_int64],
     "relearn_update_connectivity_typed": [_P, ctypes.POINTER(relearn_params), _P, _P, _P, _P,
                                           ctypes.POINTER(relearn_update_stats), _P],
     "relearn_mean_length_backward": [_P, _P, _P, _P, _P, _P, _P, _P, _P],
@@ -265,11 +265,11 @@ def relearn_update_connectivity_typed(ctx, prm, vac_ax, vac_de_exc, vac_de_inh, 
     return s.as_dict() if s is not None else None
 
 
-def relearn_debug_stall_reduce(ctx, tile):
+def relearn_debug_stall_scan(ctx, tile):
     """Testing hook: in the next bottom-up update of ctx, prefix tile `tile` publishes
     nothing, so that update's bounded waits run out (RELEARN_ERR_TIMEOUT)."""
-    _raise(ctx, lib().relearn_debug_stall_reduce(ctx.handle, int(tile)),
-           "relearn_debug_stall_reduce")
+    _raise(ctx, lib().relearn_debug_stall_scan(ctx.handle, int(tile)),
+           "relearn_debug_stall_scan")
 
 
 def relearn_build_octree_batch(ctx, offsets, x, y, z, vac_de=None, stream=None):

@@ -52,7 +52,7 @@ def test_host_argument_errors_need_no_gpu(L):
     assert L.relearn_mean_length_backward(None, None, None, None, None, None, None, None,
                                           None) == relearn.ERR_INVALID_ARG
     assert L.relearn_deliver_rates(None, None, 1, 0, None, None) == relearn.ERR_INVALID_ARG
-    assert L.relearn_debug_stall_reduce(None, 0) == relearn.ERR_INVALID_ARG
+    assert L.relearn_debug_stall_scan(None, 0) == relearn.ERR_INVALID_ARG
     ops = ctypes.c_int64()
     assert L.relearn_peak_probe(1, 0, None, 1, ctypes.byref(ops), None) == relearn.ERR_INVALID_ARG
     assert L.relearn_peak_probe(1, 1, None, 1, ctypes.byref(ops), None) == relearn.ERR_INVALID_ARG

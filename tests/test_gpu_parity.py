@@ -416,16 +416,16 @@ def test_capacity_overflow_is_reported_and_nothing_applied():
 
 
 def test_bounded_wait_timeout_is_reported_and_nothing_applied():
-    """The bottom-up update's single-pass prefix waits, bounded, for the sums of the
-    tiles before it. With one tile made never to publish (a flag nothing sets), the
-    waits run out: the update reports RELEARN_ERR_TIMEOUT within seconds, applies
-    nothing, and the context stays usable (its next update equals a fresh one's)."""
+    """The query setup's single-pass scan waits, bounded, for the sums of the tiles
+    before it. With one tile made never to publish (a flag nothing sets), the waits run
+    out: the update reports RELEARN_ERR_TIMEOUT within seconds, applies nothing, and
+    the context stays usable (its next update equals a fresh one's)."""
     import time
     from paper_2509_26193_gb300 import relearn as R
     net = workloads.gaussian_clusters(n=20000, clusters=4, side=2000, std=150, seed=81,
                                       sigma=300.0)
     g = GpuNet(net)
-    R.relearn_debug_stall_reduce(g.ctx, 3)
+    R.relearn_debug_stall_scan(g.ctx, 1)
     t0 = time.time()
     with pytest.raises(R.RelearnError) as ei:
         g.update(step=0)
