@@ -6,6 +6,9 @@
 // accepts them all; an over-requested target accepts a request iff fewer than
 // vac_de other requests to it have a smaller (priority, source, element) key,
 // which is the same set as sorting by that key and taking the first vac_de.
+// Requests are numbered in (source id, element) order, so that key orders exactly
+// like the 64-bit (priority << 32 | request number), which the scatter stores in the
+// target's bucket: ranking a request reads its bucket once, in order.
 //
 // The store is the synapse multiset. Updates append their new synapses; the
 // canonical order (source, then target) with an out-row pointer array and an
@@ -48,34 +51,30 @@ __global__ void accept_count_kernel(const int32_t *d_Q, const int32_t *__restric
     }
 }
 
+__device__ __forceinline__ uint64_t request_key(uint32_t prio, int64_t r)
+{
+    return ((uint64_t)prio << 32) | (uint64_t)(uint32_t)r;
+}
+
 __global__ void accept_scatter_kernel(const int32_t *d_Q, const int32_t *__restrict__ req_tgt,
+                                      const uint32_t *__restrict__ prio,
                                       const int32_t *__restrict__ toff,
-                                      int32_t *__restrict__ tfill, int32_t *__restrict__ bucket)
+                                      int32_t *__restrict__ tfill, uint64_t *__restrict__ bucket)
 {
     const int64_t Q = *d_Q;
     GRID_STRIDE(r, Q)
     {
         int32_t t = req_tgt[r];
         if (t < 0) continue;
-        bucket[toff[t] + atomicAdd(&tfill[t], 1)] = (int32_t)r;
+        bucket[toff[t] + atomicAdd(&tfill[t], 1)] = request_key(prio[r], r);
     }
 }
 
-__device__ __forceinline__ bool key_less(uint32_t pa, int32_t sa, int32_t ea, uint32_t pb,
-                                         int32_t sb, int32_t eb)
-{
-    if (pa != pb) return pa < pb;
-    if (sa != sb) return sa < sb;
-    return ea < eb;
-}
-
-__global__ void accept_decide_kernel(const int32_t *d_Q, const int32_t *__restrict__ req_src,
-                                     const int32_t *__restrict__ req_elem,
-                                     const int32_t *__restrict__ req_tgt,
+__global__ void accept_decide_kernel(const int32_t *d_Q, const int32_t *__restrict__ req_tgt,
                                      const uint32_t *__restrict__ prio,
                                      const int32_t *__restrict__ tcnt,
                                      const int32_t *__restrict__ toff,
-                                     const int32_t *__restrict__ bucket,
+                                     const uint64_t *__restrict__ bucket,
                                      const int32_t *__restrict__ vac_de,
                                      uint8_t *__restrict__ acc, int32_t *__restrict__ flag,
                                      int64_t *declined)
@@ -93,14 +92,10 @@ __global__ void accept_decide_kernel(const int32_t *d_Q, const int32_t *__restri
             if (rt <= v) {
                 a = 1;
             } else if (v > 0) {
-                const uint32_t pr = prio[r];
-                const int32_t sr = req_src[r], er = req_elem[r];
+                const uint64_t kr = request_key(prio[r], r); // keys are distinct
+                const uint64_t *bk = bucket + toff[t];
                 int32_t below = 0;
-                const int32_t b0 = toff[t];
-                for (int32_t k = 0; k < rt && below < v; ++k) {
-                    int32_t o = bucket[b0 + k];
-                    if (o != r && key_less(prio[o], req_src[o], req_elem[o], pr, sr, er)) ++below;
-                }
+                for (int32_t k = 0; k < rt && below < v; ++k) below += bk[k] < kr ? 1 : 0;
                 a = below < v ? 1 : 0;
             }
             dec += a ? 0 : 1;
@@ -382,11 +377,11 @@ cudaError_t accept_requests(relearn_ctx *c, const relearn_params &p, const int32
                                             c->d_req_prio, c->d_tcnt, p.seed, (uint32_t)p.step);
     note_launch();
     if ((e = scan_exclusive(c->d_tcnt, c->d_toff, n + 1, nullptr, nullptr, c->scan, st))) return e;
-    accept_scatter_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_tgt, c->d_toff, c->d_tfill,
-                                              c->d_bucket);
+    accept_scatter_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_tgt, c->d_req_prio, c->d_toff,
+                                              c->d_tfill, c->d_bucket);
     note_launch();
-    accept_decide_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_src, c->d_req_elem, c->d_req_tgt,
-                                             c->d_req_prio, c->d_tcnt, c->d_toff, c->d_bucket,
+    accept_decide_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_tgt, c->d_req_prio, c->d_tcnt,
+                                             c->d_toff, c->d_bucket,
                                              vac_de, c->d_req_acc, c->d_newpos,
                                              c->d_i64 + I64_DECLINED);
     note_launch();
