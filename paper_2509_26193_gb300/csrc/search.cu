@@ -617,16 +617,20 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                 if (S > 0.0) {
                     uint32_t u = philox_x((uint32_t)i, a.step, (uint32_t)e << 8, 0u, a.seed);
                     const double tgt = (double)u * 2.3283064365386963e-10 * S;
-                    int lo = 0, hi = nck - 1; // last checkpoint whose sum <= u * S
+                    // last checkpoint whose running total, formed as the draw walk forms
+                    // it (FP32 sum - compensation), does not exceed u * S: the walk from it
+                    // never starts past its answer
+                    const float ftgt = (float)tgt;
+                    int lo = 0, hi = nck - 1;
                     while (lo < hi) {
                         const int mid = (lo + hi + 1) >> 1;
-                        if ((double)ckc[mid] - (double)ckk[mid] <= tgt)
+                        if (__fsub_rn(ckc[mid], ckk[mid]) <= ftgt)
                             lo = mid;
                         else
                             hi = mid - 1;
                     }
                     int32_t k = find_root(a.nodes, ckp[lo], root_end, ckc[lo], ckk[lo], x,
-                                          self_node, thr0, k2, k2sh, (float)tgt);
+                                          self_node, thr0, k2, k2sh, ftgt);
                     if (k < 0) // u * S rounded up to S past the last weighted candidate
                         k = find_root(a.nodes, root + 1, root_end, 0.0f, 0.0f, x, self_node,
                                       thr0, k2, k2sh, __int_as_float(0x7f800000));
