@@ -191,6 +191,9 @@ __device__ int32_t lane_walk(const LenArgs &a, const Src &s, int32_t end, uint32
 #ifndef RELEARN_LEN_BWD_MIN_BLOCKS
 #define RELEARN_LEN_BWD_MIN_BLOCKS 5 // the adjoint's warp sums need more than 40 registers
 #endif
+// The forward pass at 6 blocks per SM (its three compensated sums need the
+// registers: 8 blocks took the 2^18-neuron forward pass from 2.46 to 3.08 ms), the
+// adjoint at 5 (6 blocks: 6.08 -> 6.32 ms).
 template <bool kBack>
 __global__ void __launch_bounds__(256, kBack ? RELEARN_LEN_BWD_MIN_BLOCKS : 6)
     length_kernel(LenArgs a)
@@ -259,8 +262,7 @@ __global__ void __launch_bounds__(256, kBack ? RELEARN_LEN_BWD_MIN_BLOCKS : 6)
                 float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
                 int2 t = make_int2(p + 1, 0);
                 if (run) {
-                    g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[p].g));
-                    t = __ldg(reinterpret_cast<const int2 *>(&a.nodes[p].t));
+                    load_node(&a.nodes[p], g, t); // one 256-bit read
                 }
                 const float rx = __fsub_rn(s.x.x, g.x), ry = __fsub_rn(s.x.y, g.y),
                             rz = __fsub_rn(s.x.z, g.z);
@@ -292,8 +294,9 @@ __global__ void __launch_bounds__(256, kBack ? RELEARN_LEN_BWD_MIN_BLOCKS : 6)
         } else {
             int32_t p = 1, skip = on_src ? 0 : 0x7fffffff;
             while (p < root_end) {
-                const float4 g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[p].g));
-                const int2 t = __ldg(reinterpret_cast<const int2 *>(&a.nodes[p].t));
+                float4 g;
+                int2 t;
+                load_node(&a.nodes[p], g, t); // one 256-bit read
                 const float rx = __fsub_rn(s.x.x, g.x), ry = __fsub_rn(s.x.y, g.y),
                             rz = __fsub_rn(s.x.z, g.z);
                 const float D = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, __fmul_rn(rz, rz)));

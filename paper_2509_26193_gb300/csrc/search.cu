@@ -859,17 +859,19 @@ __device__ __forceinline__ int split_walk(const SearchArgs &a, SplitLists &L, in
     }
     __syncwarp();
     // FP64 inclusive prefix in pre-order: lane k sums its block of ranges from zero
-    // (blk); its block starts at the left-to-right sum of blocks 0 .. k-1, and the
-    // prefix at position q of the block is start + (the block's running sum), so the
-    // last entry of block k equals block k + 1's start (the prefix is monotone)
+    // (blk); its block starts at the sum of blocks 0 .. k-1 (an exclusive warp scan in
+    // five steps: GB300 has little FP64 throughput), and the prefix at position q of
+    // the block is start + (the block's running sum)
     const int per = (n_rec + 31) >> 5;
     const int q0 = min(lane * per, n_rec), q1 = min(q0 + per, n_rec);
     double blk = 0.0;
     for (int q = q0; q < q1; ++q) blk += (double)L.part[L.ord[q]];
-    double start = 0.0;
-    for (int j = 0; j < 31; ++j) {
-        const double t = __shfl_sync(0xffffffffu, blk, j);
-        if (j < lane) start += t;
+    double start = __shfl_up_sync(0xffffffffu, blk, 1);
+    if (lane == 0) start = 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, start, o);
+        if (lane >= o) start += t;
     }
     L.start[lane] = start;
     const int nb = (n_rec + per - 1) / per;
