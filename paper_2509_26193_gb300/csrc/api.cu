@@ -338,7 +338,7 @@ relearn_status relearn_build_octree(relearn_ctx *c, int64_t n, const float *x, c
     if (reset_store) {
         CK(cudaMemsetAsync(c->d_i32 + I32_NSYN, 0, sizeof(int32_t), st), "store reset");
         CK(cudaMemsetAsync(c->d_i64 + I64_NSYN, 0, sizeof(int64_t), st), "store reset");
-        CK(rebuild_views(c, st), "views");
+        c->canonical = false; // an empty store; its views are formed when first needed
     }
     c->built = true;
     c->diag_valid = false;
@@ -386,7 +386,7 @@ relearn_status relearn_build_octree_batch(relearn_ctx *c, int32_t num_networks,
     if (reset_store) {
         CK(cudaMemsetAsync(c->d_i32 + I32_NSYN, 0, sizeof(int32_t), st), "store reset");
         CK(cudaMemsetAsync(c->d_i64 + I64_NSYN, 0, sizeof(int64_t), st), "store reset");
-        CK(rebuild_views(c, st), "views");
+        c->canonical = false; // an empty store; its views are formed when first needed
     }
     c->built = true;
     c->diag_valid = false;

@@ -208,7 +208,6 @@ cudaError_t accept_requests(relearn_ctx *c, const relearn_params &p, const int32
                             cudaStream_t st);
 cudaError_t apply_requests(relearn_ctx *c, int32_t *vac_ax, int32_t *vac_de, const uint8_t *type,
                            cudaStream_t st);
-cudaError_t rebuild_views(relearn_ctx *c, cudaStream_t st);
 // Typed dendrite pools: out[i] = vac_ax[i] where type[i] == kind, else 0; and back.
 cudaError_t select_type(relearn_ctx *c, const int32_t *vac_ax, const uint8_t *type, int kind,
                         int32_t *out, cudaStream_t st);

@@ -156,19 +156,6 @@ __global__ void apply_kernel(const int32_t *d_Q, const int32_t *d_new, const int
 }
 
 // ---------------------------------------------------------------- store
-__global__ void make_keys_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ src,
-                                 const int32_t *__restrict__ tgt,
-                                 const int8_t *__restrict__ sign, int bits,
-                                 uint64_t *__restrict__ key, int32_t *__restrict__ val)
-{
-    const int64_t m = *d_nsyn;
-    GRID_STRIDE(k, m)
-    {
-        key[k] = ((uint64_t)(uint32_t)src[k] << bits) | (uint32_t)tgt[k];
-        val[k] = sign[k];
-    }
-}
-
 __global__ void unpack_keys_kernel(const int32_t *d_nsyn, const uint64_t *__restrict__ key,
                                    const int32_t *__restrict__ val, int bits,
                                    int32_t *__restrict__ src, int32_t *__restrict__ tgt,
@@ -187,24 +174,88 @@ __global__ void unpack_keys_kernel(const int32_t *d_nsyn, const uint64_t *__rest
 
 __global__ void degree_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ src,
                               const int32_t *__restrict__ tgt, int32_t *__restrict__ out_cnt,
-                              int32_t *__restrict__ in_cnt, uint32_t *__restrict__ key32,
-                              int32_t *__restrict__ idx)
+                              int32_t *__restrict__ in_cnt)
 {
     const int64_t m = *d_nsyn;
     GRID_STRIDE(k, m)
     {
         atomicAdd(&out_cnt[src[k]], 1);
         atomicAdd(&in_cnt[tgt[k]], 1);
-        key32[k] = (uint32_t)tgt[k];
-        idx[k] = (int32_t)k;
     }
 }
 
-__global__ void in_view_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ order,
-                               int32_t *__restrict__ in_syn)
+// The canonical order without a global sort: each synapse goes to its source's row
+// (any order within the row), then takes its rank in the row by (target, place in
+// the row). Rows are short (a neuron's bound elements), so ranking by counting is
+// cheaper than sorting the whole store; equal (source, target) records are
+// identical (the sign follows the source), so their order does not matter.
+__global__ void row_scatter_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ src,
+                                   const int32_t *__restrict__ tgt, const int8_t *__restrict__ sign,
+                                   const int32_t *__restrict__ out_ptr, int32_t *__restrict__ fill,
+                                   int32_t *__restrict__ row_src, int32_t *__restrict__ row_tgt,
+                                   int32_t *__restrict__ row_sign)
 {
     const int64_t m = *d_nsyn;
-    GRID_STRIDE(k, m) in_syn[k] = order[k];
+    GRID_STRIDE(k, m)
+    {
+        const int32_t s = src[k];
+        const int32_t r = out_ptr[s] + atomicAdd(&fill[s], 1);
+        row_src[r] = s;
+        row_tgt[r] = tgt[k];
+        row_sign[r] = sign[k];
+    }
+}
+
+__global__ void row_rank_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ row_src,
+                                const int32_t *__restrict__ row_tgt,
+                                const int32_t *__restrict__ row_sign,
+                                const int32_t *__restrict__ out_ptr, int32_t *__restrict__ src,
+                                int32_t *__restrict__ tgt, int8_t *__restrict__ sign)
+{
+    const int64_t m = *d_nsyn;
+    GRID_STRIDE(r, m)
+    {
+        const int32_t s = row_src[r], t = row_tgt[r];
+        const int32_t b = out_ptr[s], e = out_ptr[s + 1];
+        int32_t rank = 0;
+        for (int32_t j = b; j < e; ++j) {
+            const int32_t tj = row_tgt[j];
+            rank += (tj < t || (tj == t && j < r)) ? 1 : 0;
+        }
+        const int32_t w = b + rank;
+        src[w] = s;
+        tgt[w] = t;
+        sign[w] = (int8_t)row_sign[r];
+    }
+}
+
+// In-view: synapse numbers k (canonical order) grouped by target, each row ordered by
+// k (i.e. by source), by the same scatter-then-rank.
+__global__ void in_scatter_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ tgt,
+                                  const int32_t *__restrict__ in_ptr, int32_t *__restrict__ fill,
+                                  int32_t *__restrict__ row_k)
+{
+    const int64_t m = *d_nsyn;
+    GRID_STRIDE(k, m)
+    {
+        const int32_t t = tgt[k];
+        row_k[in_ptr[t] + atomicAdd(&fill[t], 1)] = (int32_t)k;
+    }
+}
+
+__global__ void in_rank_kernel(const int32_t *d_nsyn, const int32_t *__restrict__ tgt,
+                               const int32_t *__restrict__ in_ptr,
+                               const int32_t *__restrict__ row_k, int32_t *__restrict__ in_syn)
+{
+    const int64_t m = *d_nsyn;
+    GRID_STRIDE(r, m)
+    {
+        const int32_t k = row_k[r], t = tgt[k];
+        const int32_t b = in_ptr[t], e = in_ptr[t + 1];
+        int32_t rank = 0;
+        for (int32_t j = b; j < e; ++j) rank += row_k[j] < k ? 1 : 0;
+        in_syn[b + rank] = k;
+    }
 }
 
 // ---------------------------------------------------------------- deletion
@@ -388,49 +439,39 @@ cudaError_t accept_requests(relearn_ctx *c, const relearn_params &p, const int32
     return cudaGetLastError();
 }
 
+// The store in canonical order (source, then target) with its views: out-row
+// pointers, in-row pointers and the in-view. Counting pass, two scans, then one
+// scatter and one in-row ranking per side (see row_scatter_kernel).
 cudaError_t canonicalise_store(relearn_ctx *c, cudaStream_t st)
 {
     cudaError_t e;
-    const int bits = id_bits(c->max_neurons);
-    const int32_t *dm = c->d_i32 + I32_NSYN;
-    const unsigned gs = grid_for(c->max_synapses, 256, c->num_sms);
-    make_keys_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_syn_tgt, c->d_syn_sign, bits,
-                                         c->d_key, c->d_val);
-    note_launch();
-    int which = 0;
-    if ((e = radix_sort_u64(c->d_key, c->d_key_alt, c->d_val, c->d_val_alt, c->max_synapses, dm,
-                            2 * bits, c->sort, st, &which)))
-        return e;
-    unpack_keys_kernel<<<gs, 256, 0, st>>>(dm, which ? c->d_key_alt : c->d_key,
-                                           which ? c->d_val_alt : c->d_val, bits, c->d_syn_src,
-                                           c->d_syn_tgt, c->d_syn_sign);
-    note_launch();
-    c->canonical = true;
-    return rebuild_views(c, st);
-}
-
-cudaError_t rebuild_views(relearn_ctx *c, cudaStream_t st)
-{
-    cudaError_t e;
     const int64_t n = c->n;
-    const int bits = id_bits(c->max_neurons);
     const int32_t *dm = c->d_i32 + I32_NSYN;
     const unsigned gs = grid_for(c->max_synapses, 256, c->num_sms);
-    int32_t *out_cnt = c->d_cnt, *in_cnt = c->d_tcnt;
+    int32_t *out_cnt = c->d_cnt, *in_cnt = c->d_tcnt, *fill = c->d_need_ax;
+    int32_t *row_src = c->d_val, *row_sign = c->d_val_alt;
+    int32_t *row_tgt = reinterpret_cast<int32_t *>(c->d_key32);
+    int32_t *row_k = reinterpret_cast<int32_t *>(c->d_key32_alt);
     if ((e = cudaMemsetAsync(out_cnt, 0, (n + 1) * sizeof(int32_t), st))) return e;
     if ((e = cudaMemsetAsync(in_cnt, 0, (n + 1) * sizeof(int32_t), st))) return e;
-    degree_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_syn_tgt, out_cnt, in_cnt, c->d_key32,
-                                      c->d_val);
+    degree_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_syn_tgt, out_cnt, in_cnt);
     note_launch();
     if ((e = scan_exclusive(out_cnt, c->d_out_ptr, n + 1, nullptr, nullptr, c->scan, st)))
         return e;
     if ((e = scan_exclusive(in_cnt, c->d_in_ptr, n + 1, nullptr, nullptr, c->scan, st))) return e;
-    int which = 0;
-    if ((e = radix_sort_u32(c->d_key32, c->d_key32_alt, c->d_val, c->d_val_alt, c->max_synapses,
-                            dm, bits, c->sort, st, &which)))
-        return e;
-    in_view_kernel<<<gs, 256, 0, st>>>(dm, which ? c->d_val_alt : c->d_val, c->d_in_syn);
+    if ((e = cudaMemsetAsync(fill, 0, n * sizeof(int32_t), st))) return e;
+    row_scatter_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_src, c->d_syn_tgt, c->d_syn_sign,
+                                           c->d_out_ptr, fill, row_src, row_tgt, row_sign);
     note_launch();
+    row_rank_kernel<<<gs, 256, 0, st>>>(dm, row_src, row_tgt, row_sign, c->d_out_ptr,
+                                        c->d_syn_src, c->d_syn_tgt, c->d_syn_sign);
+    note_launch();
+    if ((e = cudaMemsetAsync(fill, 0, n * sizeof(int32_t), st))) return e;
+    in_scatter_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_tgt, c->d_in_ptr, fill, row_k);
+    note_launch();
+    in_rank_kernel<<<gs, 256, 0, st>>>(dm, c->d_syn_tgt, c->d_in_ptr, row_k, c->d_in_syn);
+    note_launch();
+    c->canonical = true;
     return cudaGetLastError();
 }
 
@@ -499,7 +540,10 @@ cudaError_t delete_synapses(relearn_ctx *c, const relearn_params &p, const int32
     unpack_keys_kernel<<<gs, 256, 0, st>>>(dm, c->d_key, c->d_val, bits, c->d_syn_src,
                                            c->d_syn_tgt, c->d_syn_sign);
     note_launch();
-    return rebuild_views(c, st);
+    // the kept synapses are in canonical order; their views are rebuilt when an
+    // operation next needs them (the next update appends anyway)
+    c->canonical = false;
+    return cudaGetLastError();
 }
 
 namespace {
