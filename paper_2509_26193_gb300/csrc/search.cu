@@ -692,7 +692,12 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
 // restarts as in the union kernel. The candidates and their order are the union
 // kernel's; only the association of the FP32/FP64 sums differs, so a draw can
 // differ from the union kernel's only within rounding of a cumulative boundary.
-constexpr int kSplitRanges = 512; // ranges per source (the list stops growing there)
+// Ranges per source (the list stops growing there). The lists of a block's 8 warps
+// (46.6 KB at 448 ranges) decide how much of the SM's 256 KB stays L1 at 4 blocks per
+// SM: 512 ranges (53 KB per block) left about 28 KB of L1 and the split updates of the
+// clustered benchmark took 1.50 / 0.52 ms, 448 and 400 ranges leave about 60 KB:
+// 1.22 / 0.43 ms; 320 ranges 1.66 ms (lanes idle once the list is full).
+constexpr int kSplitRanges = 448;
 constexpr int kSplitMinRest = 32; // a rest of fewer nodes is not handed out
 
 // The source's candidates in [b, e), compensated sum from zero, until the running
