@@ -51,6 +51,7 @@ struct relearn_ctx {
     int num_sms = 0;
     // resident blocks per SM: [2 * batched + diagnostics][union, split]
     int search_occ[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    int split_occ[2][33] = {};  // split kernel blocks per SM, by network kind and capacity / 32
     int64_t max_neurons = 0, max_synapses = 0, max_searches = 0, max_nodes = 0;
     int32_t max_nets = 1; // networks one build may hold
     int32_t num_nets = 1; // networks in the current tree

@@ -197,6 +197,7 @@ struct SearchArgs {
     int spread_depth;  // cut depth of union pieces (-1: the default by source density)
     int64_t n_total;   // neurons of all networks
     int32_t split_below; // with forced_group 0: split kernel for at most this many sources
+    int split_cap;       // ranges per source in the split kernel (split_capacity)
     // deferred restarts (RELEARN_FLAG_REGROUP): searches whose first draw is an inner
     // node are queued here and finished after a sort by that node (subtree order)
     int defer;
@@ -692,12 +693,15 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
 // restarts as in the union kernel. The candidates and their order are the union
 // kernel's; only the association of the FP32/FP64 sums differs, so a draw can
 // differ from the union kernel's only within rounding of a cumulative boundary.
-// Ranges per source (the list stops growing there). The lists of a block's 8 warps
-// (46.6 KB at 448 ranges) decide how much of the SM's 256 KB stays L1 at 4 blocks per
-// SM: 512 ranges (53 KB per block) left about 28 KB of L1 and the split updates of the
-// clustered benchmark took 1.50 / 0.52 ms, 448 and 400 ranges leave about 60 KB:
-// 1.22 / 0.43 ms; 320 ranges 1.66 ms (lanes idle once the list is full).
-constexpr int kSplitRanges = 448;
+// Ranges per source (the list stops growing there), chosen per launch from theta
+// (split_capacity): the frontier, and with it the number of ranges a walk hands out,
+// grows about as theta^-2. Too few ranges leave lanes idle once the list is full;
+// more cost shared memory, i.e. L1 (the SM's 256 KB hold both) and resident blocks.
+// The split updates of the clustered benchmark (updates 4 and 5), per capacity:
+// theta 0.3: 320 ranges 1.66 ms, 448 1.22 / 0.43 ms, 512 1.50 / 0.52 ms (53 KB per
+// block leave about 28 KB of L1, 448 ranges about 60 KB); theta 0.2: 448 7.11 ms,
+// 512 5.62, 640 4.20, 768 3.64 ms; theta 0.5: 320 0.56 ms, 448 0.62 ms.
+constexpr int kSplitMinCap = 320, kSplitMaxCap = 1024;
 constexpr int kSplitMinRest = 32; // a rest of fewer nodes is not handed out
 
 // The source's candidates in [b, e), compensated sum from zero, until the running
@@ -733,18 +737,38 @@ __device__ __forceinline__ int warp_sum_i(int v)
     return v;
 }
 
-// Per warp: the ranges of the current source and their order. The FP64 prefix of
-// the partial sums in pre-order is kept as 32 block starts: lane k sums the ranges
-// ord[k * per .. (k + 1) * per) on top of start[k] (see split_walk).
+// Per warp: the ranges of the current source and their order, in dynamic shared
+// memory (cap ranges). The FP64 prefix of the partial sums in pre-order is kept as 32
+// block starts: lane k sums the ranges ord[k * per .. (k + 1) * per) on top of
+// start[k] (see split_walk).
 struct SplitLists {
-    int32_t b[kSplitRanges];    // first node of each range
-    float part[kSplitRanges];   // its compensated partial sum
-    int16_t next[kSplitRanges]; // the range that follows it in pre-order (-1: last)
-    int16_t ord[kSplitRanges];  // ranges in pre-order
-    double start[32];           // prefix before each lane's block of ranges
-    int32_t give_b[32], give_e[32], give_next[32]; // hand-over slots of one step
+    double *start;                          // [32] prefix before each lane's block
+    int32_t *give_b, *give_e, *give_next;   // [32] hand-over slots of one step
+    int32_t *b;                             // [cap] first node of each range
+    float *part;                            // [cap] its compensated partial sum
+    int16_t *next;                          // [cap] the range after it in pre-order
+    int16_t *ord;                           // [cap] ranges in pre-order
+    int cap;
 };
-constexpr size_t kSplitSmem = 8 * sizeof(SplitLists); // per block of 8 warps
+__host__ __device__ constexpr size_t split_warp_bytes(int cap)
+{
+    return 32 * sizeof(double) + 3 * 32 * sizeof(int32_t) + (size_t)cap * 12;
+}
+__device__ __forceinline__ SplitLists split_lists(unsigned char *raw, int w, int cap)
+{
+    unsigned char *base = raw + (size_t)w * split_warp_bytes(cap); // 8-byte aligned
+    SplitLists L;
+    L.start = reinterpret_cast<double *>(base);
+    L.give_b = reinterpret_cast<int32_t *>(base + 32 * sizeof(double));
+    L.give_e = L.give_b + 32;
+    L.give_next = L.give_e + 32;
+    L.b = L.give_next + 32;
+    L.part = reinterpret_cast<float *>(L.b + cap);
+    L.next = reinterpret_cast<int16_t *>(L.part + cap);
+    L.ord = L.next + cap;
+    L.cap = cap;
+    return L;
+}
 
 // The inclusive prefix of the ranges in pre-order, as split_walk forms it: the
 // first position q whose prefix exceeds tgt (tgt < S), and the prefix before q.
@@ -828,7 +852,7 @@ __device__ __forceinline__ int split_walk(const SearchArgs &a, SplitLists &L, in
         if (idle == 0xffffffffu) break;
         steps += lane == 0 ? 1 : 0;
         const uint32_t spl = __ballot_sync(0xffffffffu, split);
-        const int give = min(min(__popc(idle), __popc(spl)), kSplitRanges - n_rec);
+        const int give = min(min(__popc(idle), __popc(spl)), L.cap - n_rec);
         if (give > 0) { // warp-uniform: the r-th splitting lane gives to the r-th idle lane
             const int rs = __popc(spl & lt), ri = __popc(idle & lt);
             if (split && rs < give) {
@@ -888,12 +912,11 @@ __device__ __forceinline__ int split_walk(const SearchArgs &a, SplitLists &L, in
 template <bool kBatched>
 __global__ void __launch_bounds__(256) bh_split_kernel(SearchArgs a)
 {
-    extern __shared__ __align__(16) unsigned char s_raw[]; // kSplitSmem bytes
-    SplitLists *s_lists = reinterpret_cast<SplitLists *>(s_raw);
+    extern __shared__ __align__(16) unsigned char s_raw[]; // 8 x split_warp_bytes(cap)
     const int32_t A = *a.d_A;
     if (!split_launch(a, A)) return; // bh_search_kernel serves this launch
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    SplitLists &L = s_lists[w];
+    SplitLists L = split_lists(s_raw, w, a.split_cap);
     int64_t my_evals = 0, my_steps = 0;
     int32_t root = 0;
     uint32_t thr0 = 0;
@@ -1074,6 +1097,17 @@ cudaError_t search_prepare(relearn_ctx *c, const relearn_params &p, const int32_
     return cudaGetLastError();
 }
 
+// The split kernel's ranges per source for theta: 448 at 0.3, scaled as theta^-2,
+// multiples of 32 in [kSplitMinCap, kSplitMaxCap] (theta 0: the most). Per-network
+// thetas (batched form) use the scalar theta of the parameters as the guide.
+static int split_capacity(float theta)
+{
+    if (!(theta > 0.0f)) return kSplitMaxCap;
+    const double r = 448.0 * (0.3 / theta) * (0.3 / theta);
+    const long c = 32 * std::lround(r / 32.0);
+    return (int)std::min<long>(kSplitMaxCap, std::max<long>(kSplitMinCap, c));
+}
+
 cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *vac_ax,
                        cudaStream_t st)
 {
@@ -1126,25 +1160,32 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
                                      : (a.count ? bh_search_kernel<false, true>
                                                 : bh_search_kernel<false, false>);
     void (*split)(SearchArgs) = a.net ? bh_split_kernel<true> : bh_split_kernel<false>;
-    // resident blocks per SM of both kernels, queried once per context and kernel pair
+    // resident blocks per SM of both kernels, queried once per context, kernel pair and
+    // split capacity
+    a.split_cap = split_capacity(p.theta);
+    const size_t split_smem = 8 * split_warp_bytes(a.split_cap);
     int *occ = c->search_occ[a.net ? 1 : 0];
+    int &occ_split = c->split_occ[a.net ? 1 : 0][a.split_cap / 32];
     if (occ[0] == 0) {
-        int per_sm = 0, per_sm_split = 0;
+        int per_sm = 0;
         // both counting variants have the same launch bounds
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                  &per_sm, a.net ? bh_search_kernel<true, false> : bh_search_kernel<false, false>,
                  256, 0)))
             return e;
         if ((e = cudaFuncSetAttribute(split, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kSplitSmem)))
-            return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_split, split, 256,
-                                                               kSplitSmem)))
+                                      (int)(8 * split_warp_bytes(kSplitMaxCap)))))
             return e;
         occ[0] = per_sm < 1 ? 1 : per_sm;
-        occ[1] = per_sm_split < 1 ? 1 : per_sm_split;
     }
-    const int per_sm = occ[0], per_sm_split = occ[1];
+    if (occ_split == 0) {
+        int per_sm_split = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_split, split, 256,
+                                                               split_smem)))
+            return e;
+        occ_split = per_sm_split < 1 ? 1 : per_sm_split;
+    }
+    const int per_sm = occ[0], per_sm_split = occ_split;
     // the union kernel serves 32 sources per warp; with few sources per resident warp
     // it would leave the GPU mostly idle (kernel choice and widths: see kSplitWaves)
     const int64_t warps = (int64_t)c->num_sms * per_sm * 8;
@@ -1153,7 +1194,7 @@ cudaError_t search_run(relearn_ctx *c, const relearn_params &p, const int32_t *v
     // exactly one of the two kernels does the work (each reads the source count)
     kern<<<c->num_sms * per_sm, 256, 0, st>>>(a);
     note_launch();
-    split<<<c->num_sms * per_sm_split, 256, kSplitSmem, st>>>(a);
+    split<<<c->num_sms * per_sm_split, 256, split_smem, st>>>(a);
     note_launch();
     if (a.defer) {
         // regroup the deferred restarts by drawn node, then finish them
