@@ -259,8 +259,9 @@ __device__ __forceinline__ WalkOut walk(const Node *__restrict__ nodes, int32_t 
     int32_t p = p0;
     float cum = cum0;
     while (p < end) {
-        const float4 g = __ldg(reinterpret_cast<const float4 *>(&nodes[p].g));
-        const int2 t = __ldg(reinterpret_cast<const int2 *>(&nodes[p].t));
+        float4 g;
+        int2 t;
+        load_node(&nodes[p], g, t);
         const float d2 = dist2(x, g);
         const bool has = g.w > 0.0f;
         const bool acc = has && (__float_as_uint(d2) + (uint32_t)t.y > thr0);
@@ -331,8 +332,9 @@ __device__ __forceinline__ int32_t find_root(const Node *__restrict__ nodes, int
 {
     int32_t pick = -1;
     while (p < end) {
-        const float4 g = __ldg(reinterpret_cast<const float4 *>(&nodes[p].g));
-        const int2 t = __ldg(reinterpret_cast<const int2 *>(&nodes[p].t));
+        float4 g;
+        int2 t;
+        load_node(&nodes[p], g, t);
         const float d2 = dist2(x, g);
         const bool has = g.w > 0.0f;
         const bool acc = has && (__float_as_uint(d2) + (uint32_t)t.y > thr0);
@@ -575,8 +577,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                     if (run) {
                         if ((steps & (kCkStride - 1)) == 0) checkpoint(max(p, skip));
                         ++steps;
-                        g = __ldg(reinterpret_cast<const float4 *>(&a.nodes[p].g));
-                        t = __ldg(reinterpret_cast<const int2 *>(&a.nodes[p].t));
+                        load_node(&a.nodes[p], g, t);
                     }
                     const float d2 = dist2(x, g);
                     const bool on = run && p >= skip && g.w > 0.0f;
