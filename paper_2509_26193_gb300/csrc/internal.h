@@ -103,6 +103,7 @@ struct relearn_ctx {
     uint32_t *d_req_prio = nullptr; // [max_searches]
     uint64_t *d_bucket = nullptr;   // [max_searches] request keys grouped by target
     int32_t *d_tcnt = nullptr, *d_toff = nullptr, *d_tfill = nullptr; // [n + 1]
+    int32_t *d_newpos = nullptr;    // [max_searches + 1]
     uint32_t *d_rq_key = nullptr, *d_rq_key_alt = nullptr; // [max_searches] deferred restarts
     int32_t *d_rq_val = nullptr, *d_rq_val_alt = nullptr;
     int32_t *d_rq_out = nullptr, *d_rq_src = nullptr;
@@ -142,10 +143,8 @@ struct relearn_ctx {
 
 // slots of d_i64 / d_i32
 enum { I64_Q = 0, I64_FAILED, I64_DECLINED, I64_FORMED, I64_NSYN, I64_BROKEN, I64_SCAN_TOTAL,
-       I64_NODES, I64_Q_TOTAL, I64_EVALS_TOTAL, I64_ACTIVE, I64_STEPS_TOTAL, I64_LEN_EVALS,
-       I64_ACCEPTED };
-enum { I32_N = 0, I32_Q, I32_NSYN, I32_NEW, I32_NODES, I32_WORK, I32_ACTIVE, I32_RQ, I32_BASE,
-       I32_CURSOR };
+       I64_NODES, I64_Q_TOTAL, I64_EVALS_TOTAL, I64_ACTIVE, I64_STEPS_TOTAL, I64_LEN_EVALS };
+enum { I32_N = 0, I32_Q, I32_NSYN, I32_NEW, I32_NODES, I32_WORK, I32_ACTIVE, I32_RQ, I32_BASE };
 
 namespace rl {
 

@@ -76,11 +76,11 @@ __global__ void accept_decide_kernel(const int32_t *d_Q, const int32_t *__restri
                                      const int32_t *__restrict__ toff,
                                      const uint64_t *__restrict__ bucket,
                                      const int32_t *__restrict__ vac_de,
-                                     uint8_t *__restrict__ acc, int64_t *accepted,
+                                     uint8_t *__restrict__ acc, int32_t *__restrict__ flag,
                                      int64_t *declined)
 {
     const int64_t Q = *d_Q;
-    int64_t dec = 0, took = 0;
+    int64_t dec = 0;
     GRID_STRIDE(r, Q)
     {
         int32_t t = req_tgt[r];
@@ -99,31 +99,25 @@ __global__ void accept_decide_kernel(const int32_t *d_Q, const int32_t *__restri
                 a = below < v ? 1 : 0;
             }
             dec += a ? 0 : 1;
-            took += a;
         }
         acc[r] = a;
+        flag[r] = a; // scanned by the apply step into the new synapses' positions
     }
-    for (int off = 16; off; off >>= 1) {
-        dec += __shfl_xor_sync(0xffffffffu, dec, off);
-        took += __shfl_xor_sync(0xffffffffu, took, off);
-    }
+    for (int off = 16; off; off >>= 1) dec += __shfl_xor_sync(0xffffffffu, dec, off);
     if ((threadIdx.x & 31) == 0 && dec)
         atomicAdd(reinterpret_cast<unsigned long long *>(declined), (unsigned long long)dec);
-    if ((threadIdx.x & 31) == 0 && took)
-        atomicAdd(reinterpret_cast<unsigned long long *>(accepted), (unsigned long long)took);
 }
 
 // ---------------------------------------------------------------- apply
 // New store size check: formed = *d_formed; nothing is applied on overflow. The
 // store grows here: the apply kernel writes the new synapses from *d_base (the old
-// size) on, each at a slot it claims from *d_cursor (zeroed here).
+// size) on.
 __global__ void apply_check_kernel(const int64_t *d_formed, int32_t *d_nsyn, int32_t *d_new,
                                    int32_t *d_base, int64_t *d_nsyn64, int64_t max_synapses,
-                                   int32_t *status, int64_t *d_formed_out, int32_t *d_cursor)
+                                   int32_t *status, int64_t *d_formed_out)
 {
     int64_t f = *d_formed;
     const int32_t base = *d_nsyn;
-    *d_cursor = 0;
     const bool failed = *(volatile int32_t *)status != 0; // an earlier kernel reported an error
     *d_base = base;
     if (failed || (int64_t)base + f > max_synapses) {
@@ -138,35 +132,23 @@ __global__ void apply_check_kernel(const int64_t *d_formed, int32_t *d_nsyn, int
     *d_nsyn64 = *d_nsyn;
 }
 
-// The accepted requests append their synapses at slots claimed with one atomic per
-// warp: the store's raw order is never observed (delivery sums with integer atomics;
-// deletion and exports restore the canonical order first).
 __global__ void apply_kernel(const int32_t *d_Q, const int32_t *d_new, const int32_t *d_base,
-                             int32_t *d_cursor, const int32_t *__restrict__ req_src,
+                             const int32_t *__restrict__ req_src,
                              const int32_t *__restrict__ req_tgt, const uint8_t *__restrict__ acc,
-                             const uint8_t *__restrict__ type, int32_t *vac_ax, int32_t *vac_de,
-                             int32_t *__restrict__ syn_src, int32_t *__restrict__ syn_tgt,
-                             int8_t *__restrict__ syn_sign)
+                             const int32_t *__restrict__ newpos, const uint8_t *__restrict__ type,
+                             int32_t *vac_ax, int32_t *vac_de, int32_t *__restrict__ syn_src,
+                             int32_t *__restrict__ syn_tgt, int8_t *__restrict__ syn_sign)
 {
     if (*d_new < 0) return;
     const int64_t Q = *d_Q;
     const int32_t base = *d_base;
-    const int lane = threadIdx.x & 31;
-    // the whole warp steps through the requests together, so the ballot sees all lanes
-    for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); r0 < Q;
-         r0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = r0 + lane;
-        const bool a = r < Q && acc[r];
-        const uint32_t mask = __ballot_sync(0xffffffffu, a);
-        if (!mask) continue;
-        int32_t slot0 = 0;
-        if (lane == 0) slot0 = atomicAdd(d_cursor, __popc(mask));
-        slot0 = __shfl_sync(0xffffffffu, slot0, 0);
-        if (!a) continue;
+    GRID_STRIDE(r, Q)
+    {
+        if (!acc[r]) continue;
         const int32_t s = req_src[r], t = req_tgt[r];
         atomicSub(&vac_ax[s], 1);
         atomicSub(&vac_de[t], 1);
-        const int32_t k = base + slot0 + __popc(mask & lanemask_lt());
+        const int32_t k = base + newpos[r];
         syn_src[k] = s;
         syn_tgt[k] = t;
         syn_sign[k] = type[s] ? (int8_t)-1 : (int8_t)1;
@@ -442,7 +424,6 @@ cudaError_t accept_requests(relearn_ctx *c, const relearn_params &p, const int32
     if ((e = cudaMemsetAsync(c->d_tcnt, 0, (n + 1) * sizeof(int32_t), st))) return e;
     if ((e = cudaMemsetAsync(c->d_tfill, 0, (n + 1) * sizeof(int32_t), st))) return e;
     if ((e = cudaMemsetAsync(c->d_i64 + I64_DECLINED, 0, sizeof(int64_t), st))) return e;
-    if ((e = cudaMemsetAsync(c->d_i64 + I64_ACCEPTED, 0, sizeof(int64_t), st))) return e;
     accept_count_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_src, c->d_req_elem, c->d_req_tgt,
                                             c->d_req_prio, c->d_tcnt, p.seed, (uint32_t)p.step);
     note_launch();
@@ -452,7 +433,7 @@ cudaError_t accept_requests(relearn_ctx *c, const relearn_params &p, const int32
     note_launch();
     accept_decide_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_tgt, c->d_req_prio, c->d_tcnt,
                                              c->d_toff, c->d_bucket,
-                                             vac_de, c->d_req_acc, c->d_i64 + I64_ACCEPTED,
+                                             vac_de, c->d_req_acc, c->d_newpos,
                                              c->d_i64 + I64_DECLINED);
     note_launch();
     return cudaGetLastError();
@@ -497,17 +478,21 @@ cudaError_t canonicalise_store(relearn_ctx *c, cudaStream_t st)
 cudaError_t apply_requests(relearn_ctx *c, int32_t *vac_ax, int32_t *vac_de, const uint8_t *type,
                            cudaStream_t st)
 {
+    cudaError_t e;
     const int32_t *dQ = c->d_i32 + I32_Q;
     const unsigned gq = grid_for(c->max_searches, 256, c->num_sms);
-    apply_check_kernel<<<1, 1, 0, st>>>(c->d_i64 + I64_ACCEPTED, c->d_i32 + I32_NSYN,
+    // d_newpos holds the acceptance flags (written by the acceptance step)
+    if ((e = scan_exclusive(c->d_newpos, c->d_newpos, c->max_searches, dQ,
+                            c->d_i64 + I64_SCAN_TOTAL, c->scan, st)))
+        return e;
+    apply_check_kernel<<<1, 1, 0, st>>>(c->d_i64 + I64_SCAN_TOTAL, c->d_i32 + I32_NSYN,
                                         c->d_i32 + I32_NEW, c->d_i32 + I32_BASE,
                                         c->d_i64 + I64_NSYN, c->max_synapses, c->d_status,
-                                        c->d_i64 + I64_FORMED, c->d_i32 + I32_CURSOR);
+                                        c->d_i64 + I64_FORMED);
     note_launch();
-    apply_kernel<<<gq, 256, 0, st>>>(dQ, c->d_i32 + I32_NEW, c->d_i32 + I32_BASE,
-                                     c->d_i32 + I32_CURSOR, c->d_req_src, c->d_req_tgt,
-                                     c->d_req_acc, type, vac_ax, vac_de, c->d_syn_src,
-                                     c->d_syn_tgt, c->d_syn_sign);
+    apply_kernel<<<gq, 256, 0, st>>>(dQ, c->d_i32 + I32_NEW, c->d_i32 + I32_BASE, c->d_req_src,
+                                     c->d_req_tgt, c->d_req_acc, c->d_newpos, type, vac_ax,
+                                     vac_de, c->d_syn_src, c->d_syn_tgt, c->d_syn_sign);
     note_launch();
     // new synapses sit unsorted at the end of the store until an operation needs the
     // canonical order (deletion, export); spike delivery reads the store in any order
