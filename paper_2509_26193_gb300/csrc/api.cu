@@ -275,6 +275,7 @@ relearn_status relearn_create_batched(relearn_ctx **out, int device, int64_t max
     if (e == cudaSuccess) {
         c->scan.max_blocks = scan_blocks;
         c->scan.status = c->d_status;
+        c->scan.grid_cap = scan_grid_cap(c->num_sms);
         c->sort.max_blocks = sort_blocks;
         c->sort.scan = c->scan;
         for (cudaEvent_t &ev : c->ev)

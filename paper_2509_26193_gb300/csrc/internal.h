@@ -17,6 +17,7 @@ struct ScanScratch {
                                    // states; zero between scans
     int32_t *status = nullptr;     // device status word for a wait that ran out (or NULL)
     int64_t max_blocks = 0;
+    int64_t grid_cap = 1 << 30;    // blocks a scan launches at most (the resident ones)
 };
 
 // Scratch of the LSD radix sort (per-block digit histograms, digit-major).
@@ -168,6 +169,7 @@ void note_launch();
 cudaError_t scan_exclusive(const int32_t *in, int32_t *out, int64_t max_n, const int32_t *d_count,
                            int64_t *d_total, ScanScratch &s, cudaStream_t st);
 int64_t scan_blocks_needed(int64_t max_n);
+int64_t scan_grid_cap(int num_sms);
 cudaError_t fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t st);
 
 // sort.cu -------------------------------------------------------------------

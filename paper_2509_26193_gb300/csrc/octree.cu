@@ -489,8 +489,9 @@ __device__ __forceinline__ L4 l4_block_inclusive(L4 v, L4 *total)
 constexpr int kRedItems = 4;
 constexpr int kRedTile = 256 * kRedItems;
 
-// The prefix P runs in three passes with no waiting between blocks: leaves and tile
-// sums, a scan of the tile sums in one block, then each tile's prefix.
+// The prefix P runs in passes with no waiting between blocks: leaves and tile sums,
+// then each tile's prefix (up to kRedDirect tiles each block adds up the tile sums
+// before its own; beyond that one block first scans the tile sums).
 
 // Sum of v over a block of 256 threads (every thread receives it).
 __device__ __forceinline__ L4 l4_block_sum(L4 v, L4 *wt)
@@ -562,12 +563,24 @@ __global__ void __launch_bounds__(1024)
 }
 
 // Pass 3: P over tile t = the tile's prefix + the exclusive scan of w inside the tile
-// (thread i: positions 4i .. 4i + 3 of the tile).
+// (thread i: positions 4i .. 4i + 3 of the tile). direct: tile holds the tile sums
+// and each block adds up those before its own (at most kRedDirect tiles: no pass 2,
+// and the last block writes P[n]); else tile holds the prefixes pass 2 formed.
+constexpr int64_t kRedDirect = 2048;
 __global__ void __launch_bounds__(256)
     reduce_prefix_kernel(const int32_t *__restrict__ perm, const int4 *__restrict__ posq,
                          const int32_t *__restrict__ vac_de, int64_t n,
-                         const L4 *__restrict__ tile_pre, L4 *__restrict__ P)
+                         const L4 *__restrict__ tile, L4 *__restrict__ P, bool direct)
 {
+    __shared__ L4 s_part[8];
+    L4 pre{0, 0, 0, 0};
+    if (direct) {
+        for (int64_t j = threadIdx.x; j < (int64_t)blockIdx.x; j += 256)
+            pre = l4_add(pre, tile[j]);
+        pre = l4_block_sum(pre, s_part);
+    } else {
+        pre = tile[blockIdx.x];
+    }
     const int64_t s0 = (int64_t)blockIdx.x * kRedTile + (int64_t)threadIdx.x * kRedItems;
     L4 w[kRedItems];
     L4 acc{0, 0, 0, 0};
@@ -585,12 +598,13 @@ __global__ void __launch_bounds__(256)
         acc = l4_add(acc, w[k]);
     }
     L4 tot;
-    L4 run = l4_add(tile_pre[blockIdx.x], l4_sub(l4_block_inclusive(acc, &tot), acc));
+    L4 run = l4_add(pre, l4_sub(l4_block_inclusive(acc, &tot), acc));
 #pragma unroll
     for (int k = 0; k < kRedItems; ++k) {
         if (s0 + k < n) P[s0 + k] = run;
         run = l4_add(run, w[k]);
     }
+    if (direct && threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) P[n] = l4_add(pre, tot);
 }
 
 __device__ __forceinline__ void inner_sums(Node *__restrict__ nodes, int64_t v, int64_t first,
@@ -734,11 +748,15 @@ cudaError_t octree_reduce(relearn_ctx *c, const int32_t *vac_de, cudaStream_t st
                                                             c->d_pos, c->d_posq, vac_de, n, tile);
         note_launch();
     }
-    reduce_tiles_kernel<<<1, 1024, 0, st>>>(tile, nb, P, n);
-    note_launch();
+    // up to kRedDirect tiles each prefix block adds up the tile sums before it itself
+    const bool direct = nb > 0 && nb <= kRedDirect;
+    if (!direct) {
+        reduce_tiles_kernel<<<1, 1024, 0, st>>>(tile, nb, P, n);
+        note_launch();
+    }
     if (nb > 0) {
         reduce_prefix_kernel<<<(unsigned)nb, 256, 0, st>>>(c->d_perm, c->d_posq, vac_de, n, tile,
-                                                            P);
+                                                            P, direct);
         note_launch();
     }
     reduce_nodes_kernel<<<grid_for(c->max_nodes, 256, c->num_sms), 256, 0, st>>>(

@@ -1,5 +1,7 @@
 // Device-wide exclusive scan of int32 with int64 carries, in one pass (decoupled
-// look-back): each block takes the next tile by ticket, stages it in shared memory
+// look-back): a grid of at most the resident blocks, each taking the next tile by
+// ticket until none is left (capacity-sized scans of short inputs then launch no
+// waves of idle blocks), stages it in shared memory
 // (coalesced global reads and writes), sums it, publishes the tile sum, then its
 // first warp reads the states of the 32 preceding tiles at once and adds their
 // published sums back to the nearest one that has published its inclusive prefix
@@ -200,15 +202,22 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ int32_t tile[kTile];
     __shared__ int64_t s_prefix;
     __shared__ int32_t s_t, s_last;
+    const int64_t max_tiles = max_n > 0 ? (max_n + kTile - 1) / kTile : 1;
     if (threadIdx.x == 0) s_t = atomicAdd(&flags[0], 1);
     __syncthreads();
-    const int64_t t = s_t;
     const int64_t n = bounded_count(max_n, d_count);
-    // tiles past the last element (grids are sized by capacity) have nothing to do, and
-    // no tile that has elements looks back at them
+    // tiles past the last element (capacities are sized for the largest input) have
+    // nothing to do, and no tile that has elements looks back at them
     const int64_t last_tile = n > 0 ? (n - 1) / kTile : 0;
-    if (t <= last_tile) scan_tile(in, out, n, t, last_tile, flags, agg, inc, d_total, status,
-                                  tile, s_prefix);
+    // a persistent grid: each block takes tiles by ticket until they run out (a tile
+    // only waits for smaller tickets, held by blocks already running)
+    for (int64_t t = s_t; t <= last_tile;) {
+        scan_tile(in, out, n, t, last_tile, flags, agg, inc, d_total, status, tile, s_prefix);
+        __syncthreads();
+        if (threadIdx.x == 0) s_t = atomicAdd(&flags[0], 1);
+        __syncthreads();
+        t = s_t;
+    }
     // the last block to finish clears the ticket, abort flag, counter and tile states
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -218,7 +227,7 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     if (s_last) {
         __threadfence();
-        for (int64_t j = threadIdx.x; j < (int64_t)gridDim.x; j += blockDim.x) flags[3 + j] = 0;
+        for (int64_t j = threadIdx.x; j < max_tiles; j += blockDim.x) flags[3 + j] = 0;
         if (threadIdx.x == 0) {
             flags[0] = 0;
             flags[1] = 0;
@@ -237,16 +246,28 @@ __global__ void fill_kernel(int32_t *p, int32_t v, int64_t n)
 
 int64_t scan_blocks_needed(int64_t max_n) { return (max_n + kTile - 1) / kTile; }
 
+int64_t scan_grid_cap(int num_sms)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel, kThreads, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    return (int64_t)per_sm * (num_sms > 0 ? num_sms : 1);
+}
+
 cudaError_t scan_exclusive(const int32_t *in, int32_t *out, int64_t max_n, const int32_t *d_count,
                            int64_t *d_total, ScanScratch &s, cudaStream_t st)
 {
     int64_t nb = scan_blocks_needed(max_n);
     if (nb == 0) nb = 1;
     if (nb > s.max_blocks) return cudaErrorInvalidValue;
+    // a grid of resident blocks at most: they take the tiles by ticket
+    const int64_t grid = nb < s.grid_cap ? nb : s.grid_cap;
     // s.flags is zero here: zeroed at allocation and cleared by every scan's last block
-    scan_kernel<<<(unsigned)nb, kThreads, 0, st>>>(in, out, max_n, d_count, s.flags,
-                                                   s.block_sums, s.block_sums + nb, d_total,
-                                                   s.status);
+    scan_kernel<<<(unsigned)grid, kThreads, 0, st>>>(in, out, max_n, d_count, s.flags,
+                                                     s.block_sums, s.block_sums + nb, d_total,
+                                                     s.status);
     note_launch();
     return cudaGetLastError();
 }
