@@ -319,7 +319,35 @@ __device__ __forceinline__ void union_step(const Node *__restrict__ nodes, int32
         skip = t.x;
         if (p != self_node) kahan_add(cum, comp, attraction(g.w, d2, k2, k2sh));
     }
-    p = __any_sync(0xffffffffu, on && !pass) ? p + 1 : max(t.x, p + 1);
+    // escapes lie past their node in every well-formed tree; the caller checks that each
+    // block of steps advances, which keeps the walk finite regardless
+    p = __any_sync(0xffffffffu, on && !pass) ? p + 1 : t.x;
+}
+
+// One step of several union walks in one warp (lane groups gmask; see
+// bh_search_kernel): a group whose walk has ended sits on the sentinel node at
+// root_end, which has no count, and its escape is clamped back to root_end.
+template <bool kCount>
+__device__ __forceinline__ void group_step(const Node *__restrict__ nodes, int32_t &p,
+                                           int32_t &skip, float &cum, float &comp,
+                                           int32_t &own, int32_t &gst, float3 x,
+                                           int32_t self_node, uint32_t thr0, float k2,
+                                           float k2sh, uint32_t gmask, int32_t root_end)
+{
+    float4 g;
+    int2 t;
+    if (kCount) gst += p < root_end ? 1 : 0;
+    load_node(&nodes[p], g, t);
+    const float d2 = dist2(x, g);
+    const bool on = p >= skip && g.w > 0.0f;
+    const bool pass = __float_as_uint(d2) + (uint32_t)t.y > thr0;
+    if (kCount) own += on ? 1 : 0;
+    if (on && pass) {
+        skip = t.x;
+        if (p != self_node) kahan_add(cum, comp, attraction(g.w, d2, k2, k2sh));
+    }
+    const uint32_t down = __ballot_sync(0xffffffffu, on && !pass) & gmask;
+    p = min(down ? p + 1 : t.x, root_end);
 }
 
 // Draw on the root frontier from a checkpoint: the lane's own walk with pass 1's
@@ -548,6 +576,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                 // one walk per warp: every lane steps together, no group masks
                 while (p < root_end) {
                     checkpoint(max(p, skip));
+                    const int32_t p_blk = p;
                     int k = 0;
                     if constexpr (!kBatched) {
                         // four steps per test: nodes root_end .. root_end + 2 are
@@ -567,8 +596,30 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
                                                thr0, k2, k2sh);
                     }
                     steps += k;
+                    if (p <= p_blk) break; // no progress: only a malformed tree
                 }
                 if (p > root_end) steps -= p - root_end; // the sentinels' steps
+            } else if constexpr (!kBatched) {
+                // several walks per warp (lane groups gmask) in the same blocks of four
+                // steps per test: a group that has finished parks on the sentinel at
+                // root_end (no count; its escape is clamped back to root_end)
+                int32_t gst = 0; // this group's own steps (counted with kCount only)
+                while (__any_sync(0xffffffffu, p < root_end)) {
+                    if (p < root_end) checkpoint(max(p, skip));
+                    const int32_t p_blk = p;
+                    int k = 0;
+#pragma unroll 1
+                    for (; k < kCkStride && __any_sync(0xffffffffu, p < root_end); k += 4) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            group_step<kCount>(a.nodes, p, skip, cum, comp, own, gst, x,
+                                               self_node, thr0, k2, k2sh, gmask, root_end);
+                    }
+                    steps += k;
+                    // no progress: only a malformed tree
+                    if (__any_sync(0xffffffffu, p < root_end && p <= p_blk)) break;
+                }
+                steps = gst;
             } else {
                 while (__any_sync(0xffffffffu, p < root_end)) {
                     const bool run = p < root_end; // uniform within the group
