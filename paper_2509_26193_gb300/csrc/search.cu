@@ -49,14 +49,19 @@ constexpr int kCkStride = 128; // warp steps between checkpoints (times 2^k once
 constexpr int kMaxCk = 128;    // checkpoints kept per lane
 constexpr float kTiny = 8.673617e-19f; // 2^-60
 // Walks per warp (see bh_search_kernel): the warp's 32 sources are cut into pieces at
-// the boundaries of cells of some depth, and each piece walks one union. The more
-// neurons search, the closer consecutive sources are, and the coarser the cut can be
-// before a union spans sources too far apart: depth 2 when at least kDenseTenths / 10
-// of the neurons search, depth 3 from kMidTenths / 10, else depth 4. Per-update sweeps
-// (2^20-neuron clustered network, first three updates, 86 / 40 / 15 % of the neurons
-// searching): depth 2 7.06 / 4.23 / 2.87 ms, depth 3 7.07 / 3.91 / 2.53 ms, depth 4
-// 7.20 / 4.00 / 2.35 ms; a batch of 256 uniform networks, 86 % searching: depth 2
-// 234.9 ms, depth 4 274.2 ms.
+// the boundaries of cells of some depth, and each piece walks one union. With one
+// network the warp's pieces step in blocks of four like a single union, so fine cuts
+// cost little: depth kCutSingle (cells of 1/64 of the domain's edge). Sweep on the
+// 2^20-neuron clustered network (first three updates, 86 / 40 / 15 % of the neurons
+// searching): depth 2 6.85 / 4.12 / 2.74 ms, depth 4 6.87 / 3.78 / 2.27, depth 5
+// 6.83 / 3.78 / 2.16, depth 6 6.77 / 3.78 / 2.16, depth 7 7.24 / 4.10 / 2.81,
+// depth 10 13.65 / 6.84 / 4.05. With several networks (pieces stepped one step per
+// test) the cut follows the share of neurons searching: the more search, the closer
+// consecutive sources are, and the coarser the cut can be before a union spans
+// sources too far apart: depth 2 when at least kDenseTenths / 10 of the neurons
+// search, depth 3 from kMidTenths / 10, else depth 4 (a batch of 256 uniform
+// networks, 86 % searching: depth 2 234.9 ms, depth 4 274.2 ms).
+constexpr int kCutSingle = 6;
 constexpr int kCutDense = 2, kCutMid = 3, kCutSparse = 4, kDenseTenths = 6, kMidTenths = 3;
 // The default also looks at how many sources the update has, per resident warp of
 // the union kernel (W = 7,296 on 152 SMs). Per-update sweeps on the 2^20-neuron
@@ -516,6 +521,7 @@ __global__ void __launch_bounds__(256, RELEARN_SEARCH_MIN_BLOCKS) bh_search_kern
             code = __shfl_sync(0xffffffffu, code, live ? lane : last);
             const uint32_t nxt = __shfl_down_sync(0xffffffffu, code, 1);
             const int depth = a.spread_depth >= 0                          ? a.spread_depth
+                              : !kBatched                                   ? kCutSingle
                               : (int64_t)A * 10 >= kDenseTenths * a.n_total ? kCutDense
                               : (int64_t)A * 10 >= kMidTenths * a.n_total   ? kCutMid
                                                                             : kCutSparse;
