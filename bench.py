@@ -445,6 +445,50 @@ class Runner:
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
+    def first_update_graph_ms(self, reps=5):
+        """Phase times of the first update from the library's events inside a captured
+        and replayed update (initial vacancies, octree build, one update without
+        diagnostics): device time without the host's launch gaps between the small
+        kernels. A deletion of every synapse after each replay (outside the graph)
+        leaves the store empty for the next."""
+        torch, R = self.torch, self.R
+        p = R.params(self.net.sigma, self.theta, self.net.seed, 0,
+                     R.FLAG_TIMING | self.extra_flags, self.group)
+        pdel = R.params(self.net.sigma, self.theta, self.net.seed, 999)
+
+        def body():
+            self.vac_ax.copy_(self.vac_ax0)
+            self.vac_de.copy_(self.vac_de0)
+            R.relearn_build_octree(self.ctx, self.x, self.y, self.z)
+            R.relearn_update_connectivity(self.ctx, p, self.vac_ax, self.vac_de, self.type)
+
+        def clear():
+            R.relearn_delete_synapses(self.ctx, pdel, self.retract, self.retract, self.vac_ax,
+                                      self.vac_de)
+
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            body()
+            clear()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            body()
+        keys = ("ms_reduce", "ms_search_kernel", "ms_accept", "ms_apply", "ms_total")
+        acc = dict.fromkeys(keys, 0.0)
+        for _ in range(reps):
+            g.replay()
+            torch.cuda.synchronize()
+            st = R.relearn_get_last_stats(self.ctx)
+            for k in keys:
+                acc[k] += st[k]
+            clear()
+        torch.cuda.synchronize()
+        R.relearn_collect_search_times(self.ctx)  # drop the replays' search events
+        return {k: v / reps for k, v in acc.items()}
+
     def close(self):
         self.ctx.close()
 
@@ -645,6 +689,7 @@ def measure_clusters(net, theta, device, args, pk, counters, regroup=False, e2e=
     torch.cuda.synchronize()
     dg = run.diag_step()
     build_ms = run.build_graph_ms() if profile else None
+    upd_graph = run.first_update_graph_ms() if profile else None
     if args.graph:
         # search-kernel times (library events) come from direct steps; the step time
         # from graph replays of the same step
@@ -659,7 +704,7 @@ def measure_clusters(net, theta, device, args, pk, counters, regroup=False, e2e=
     if args.graph:
         res.update({k: res_k[k] for k in ("kernel_ms", "kernel_launches", "launches")})
     out = {"res": res, "clocks": clk, "diag": dg, "prof": prof, "runner": run,
-           "build_graph_ms": build_ms}
+           "build_graph_ms": build_ms, "first_update_graph": upd_graph}
     if e2e and not args.no_e2e:
         if not args.graph:
             run.step(e2e=True)
@@ -733,6 +778,7 @@ def run_ours(args):
                          "ms_accept": prof["ms_accept"], "ms_apply": prof["ms_apply"],
                          "ms_build_a1_a3": prof["ms_build"],
                          "ms_build_a1_a3_graph": m["build_graph_ms"],
+                         "graph_replay": m["first_update_graph"],
                          "searches_per_s": prof["searches"] / (prof["ms_total"] / 1e3)},
         "evals_per_search_algorithmic": dg["evals_alg"] / max(dg["searches"], 1),
         "evals_per_search_made": dg["evals_dedup"] / max(dg["searches"], 1),

@@ -22,10 +22,12 @@
  *   - A context is bound to one device and is not thread-safe; calls on one
  *     context must be issued from one host thread, on streams the caller keeps
  *     ordered.
- *   - Graph capture: build, update (stats NULL, no RELEARN_FLAG_TIMING), deletion
- *     (broken NULL), delivery and the mean-length pair enqueue only device work with
- *     device-side counts, so a sequence of them can be captured into a CUDA graph and
- *     replayed. The context's host-side bookkeeping (whether the store is in canonical
+ *   - Graph capture: build, update (stats NULL), deletion (broken NULL), delivery and
+ *     the mean-length pair enqueue only device work with device-side counts, so a
+ *     sequence of them can be captured into a CUDA graph and replayed. An update
+ *     captured with RELEARN_FLAG_TIMING puts its phase events into the graph as
+ *     event-record nodes: after a replay, relearn_get_last_stats returns that
+ *     replay's phase times (of the last update captured with the flag). The context's host-side bookkeeping (whether the store is in canonical
  *     order, which diagnostics are valid) follows the captured calls, not the replays:
  *     a replayed sequence must end in the same store state its capture ended in (e.g.
  *     end with a deletion, or call relearn_get_synapses only after direct calls).

@@ -395,6 +395,19 @@ relearn_status relearn_build_octree_batch(relearn_ctx *c, int32_t num_networks,
     return RELEARN_OK;
 }
 
+// A phase event of a timed update. Under stream capture it is recorded as an
+// event-record node of the graph, so every replay records it and the phase times of
+// the last replay can be read; otherwise an ordinary record.
+static cudaError_t record_phase(cudaEvent_t ev, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    return cudaEventRecordWithFlags(ev, st,
+                                    cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                        : cudaEventRecordDefault);
+}
+
 relearn_status relearn_update_connectivity(relearn_ctx *c, const relearn_params *p,
                                            int32_t *vac_ax, int32_t *vac_de,
                                            const uint8_t *type, relearn_update_stats *stats,
@@ -412,20 +425,20 @@ relearn_status relearn_update_connectivity(relearn_ctx *c, const relearn_params 
     const bool timed = stats || (p->flags & RELEARN_FLAG_TIMING);
     c->timed = timed;
     c->length_valid = false;
-    if (timed) CK(cudaEventRecord(c->ev[0], st), "event");
+    if (timed) CK(record_phase(c->ev[0], st), "event");
     CK(octree_reduce(c, vac_de, st), "reduce");
-    if (timed) CK(cudaEventRecord(c->ev[1], st), "event");
+    if (timed) CK(record_phase(c->ev[1], st), "event");
     CK(search_prepare(c, *p, vac_ax, st), "search prepare");
-    if (timed) CK(cudaEventRecord(c->ev[2], st), "event");
+    if (timed) CK(record_phase(c->ev[2], st), "event");
     const bool ring = (p->flags & RELEARN_FLAG_TIMING) && c->nkev < 64;
-    if (ring) CK(cudaEventRecord(c->kev[c->nkev][0], st), "event");
+    if (ring) CK(record_phase(c->kev[c->nkev][0], st), "event");
     CK(search_run(c, *p, vac_ax, st), "search");
-    if (ring) CK(cudaEventRecord(c->kev[c->nkev++][1], st), "event");
-    if (timed) CK(cudaEventRecord(c->ev[3], st), "event");
+    if (ring) CK(record_phase(c->kev[c->nkev++][1], st), "event");
+    if (timed) CK(record_phase(c->ev[3], st), "event");
     CK(accept_requests(c, *p, vac_de, st), "accept");
-    if (timed) CK(cudaEventRecord(c->ev[4], st), "event");
+    if (timed) CK(record_phase(c->ev[4], st), "event");
     CK(apply_requests(c, vac_ax, vac_de, type, st), "apply");
-    if (timed) CK(cudaEventRecord(c->ev[5], st), "event");
+    if (timed) CK(record_phase(c->ev[5], st), "event");
     c->diag_valid = (p->flags & RELEARN_FLAG_DIAG) != 0;
     c->stats_valid = true;
     if (stats) return relearn_get_last_stats(c, stats);

@@ -162,6 +162,57 @@ def test_results_do_not_depend_on_search_group():
     assert np.array_equal(uev[same], sev[same])
 
 
+def test_timed_update_in_a_cuda_graph_reports_phase_times():
+    """An update captured with RELEARN_FLAG_TIMING: its phase events are nodes of the
+    graph, so after each replay relearn_get_last_stats reads that replay's phase times
+    (positive, adding up to the total), and the replay's requests equal a direct
+    update's."""
+    import torch
+    from paper_2509_26193_gb300 import relearn as R
+    net = workloads.gaussian_clusters(n=40000, clusters=5, side=2000.0, std=150.0, seed=12)
+    g = GpuNet(net)
+    va0, vd0 = g.vac_ax.clone(), g.vac_de.clone()
+    big = dev(np.full(net.n, 1 << 20, np.int32))
+    p = R.params(net.sigma, net.theta, net.seed, 3, R.FLAG_TIMING)
+    pdel = R.params(net.sigma, net.theta, net.seed, 999)
+
+    def body():
+        g.vac_ax.copy_(va0)
+        g.vac_de.copy_(vd0)
+        R.relearn_build_octree(g.ctx, g.x, g.y, g.z)
+        R.relearn_update_connectivity(g.ctx, p, g.vac_ax, g.vac_de, g.type)
+
+    def clear():
+        R.relearn_delete_synapses(g.ctx, pdel, big, big, g.vac_ax, g.vac_de)
+
+    body()
+    torch.cuda.synchronize()
+    direct = R.relearn_get_requests(g.ctx)
+    clear()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        body()
+        clear()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        body()
+    for _ in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        st = R.relearn_get_last_stats(g.ctx)
+        parts = [st[k] for k in ("ms_reduce", "ms_search", "ms_accept", "ms_apply")]
+        assert all(v > 0 for v in parts) and st["ms_total"] > 0, st
+        assert abs(sum(parts) - st["ms_total"]) <= 0.01 + 0.01 * st["ms_total"], st
+        t, a = R.relearn_get_requests(g.ctx)
+        assert np.array_equal(t, direct[0]) and np.array_equal(a, direct[1])
+        clear()
+    torch.cuda.synchronize()
+    g.close()
+
+
 def test_regrouped_restarts_are_bit_identical():
     """Two-phase search (restarts queued, sorted by their subtree, finished by a
     separate kernel) gives exactly the requests, diagnostics and acceptances of the
