@@ -607,24 +607,73 @@ __global__ void __launch_bounds__(256)
     if (direct && threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) P[n] = l4_add(pre, tot);
 }
 
+// a + b = s + e exactly (Knuth's two-sum, any magnitudes).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// r (|r| < 2^43) as hi + lo, both exact floats: hi the multiple of 2^21, lo the rest.
+__device__ __forceinline__ void split21(int64_t r, float &hi, float &lo)
+{
+    hi = __fmul_rn(__int2float_rn((int32_t)(r >> 21)), 2097152.0f);
+    lo = __uint2float_rn((uint32_t)(r & 0x1FFFFF));
+}
+
+// One centroid coordinate: the float nearest to o + (s / c) * scale for the exact
+// fixed-point sum 0 <= s <= (2^30 - 1) c, the count 1 <= c < 2^31 = cf + cl (cf the
+// float nearest to c, cl the exact rest), rc = 1 / cf rounded, and scale = 2^-k, all
+// in FP32 and integer arithmetic (GB300 runs about two FP64 lanes per clock per SM).
+// The quotient: an FP32 estimate q of s / c, corrected twice by the exact integer
+// remainder r = s - q c until -c <= r < 2c; then r / c as an unevaluated pair fh + fl
+// (fh = r * rc, fl from the exact residual r - fh c), relative error about 2^-44.
+// The coordinate: o + q scale + (fh + fl) scale summed with error-free two-sums (the
+// products by the power of two are exact) and rounded once.
+__device__ __forceinline__ float centroid_coord(int64_t s, int64_t c, float cf, float cl, float rc,
+                                                float o, float scale)
+{
+    const float sf = __fmaf_rn(__uint2float_rn((uint32_t)(s >> 32)), 4294967296.0f,
+                               __uint2float_rn((uint32_t)s));
+    int64_t q = (int64_t)__float2uint_rz(__fmul_rn(sf, rc)); // within 2^9 of s / c
+    int64_t r = s - q * c;
+    float rh, rl;
+    split21(r, rh, rl);
+    q += __float2int_rd(__fmul_rn(__fadd_rn(rh, rl), rc)); // floor(s / c), or one off
+    r = s - q * c;                                         // -c <= r < 2c
+    split21(r, rh, rl);
+    float rf, rerr;
+    two_sum(rh, rl, rf, rerr); // r = rf + rerr exactly
+    const float fh = __fmul_rn(rf, rc);
+    float e = __fmaf_rn(-fh, cf, rf); // rf - fh cf, exact
+    e = __fsub_rn(__fadd_rn(e, rerr), __fmul_rn(fh, cl));
+    const float fl = __fmul_rn(e, rc);
+    const float qa = __int2float_rn((int32_t)(q & ~(int64_t)0xFFFF)); // exact
+    const float qb = __int2float_rn((int32_t)(q & 0xFFFF));           // exact
+    float h1, e1, h2, e2, h3, e3;
+    two_sum(o, __fmul_rn(qa, scale), h1, e1);
+    two_sum(h1, __fmul_rn(qb, scale), h2, e2);
+    two_sum(h2, __fmul_rn(fh, scale), h3, e3);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), e3), __fmul_rn(fl, scale));
+    return __fadd_rn(h3, lo);
+}
+
 __device__ __forceinline__ void inner_sums(Node *__restrict__ nodes, int64_t v, int64_t first,
                                            int64_t size, const L4 *__restrict__ P,
                                            const Geom *g)
 {
-    const double ox = g->fx_lo[0], oy = g->fx_lo[1], oz = g->fx_lo[2], inv = g->fx_inv;
     const L4 s = l4_sub(P[first + size], P[first]);
     if (s.c > 0) {
-        // inv / count without an FP64 division (GB300 has little FP64 throughput): an
-        // FP32 reciprocal refined by two Newton steps in FP64 (relative error about
-        // 2^-48, far below the FP32 rounding of the centroid)
-        const double c = (double)s.c;
-        double q = (double)__frcp_rn((float)c);
-        q = fma(q, fma(-c, q, 1.0), q);
-        q = fma(q, fma(-c, q, 1.0), q);
-        const double r = inv * q;
-        nodes[v].g = NodeGeo{__double2float_rn(ox + (double)s.x * r),
-                             __double2float_rn(oy + (double)s.y * r),
-                             __double2float_rn(oz + (double)s.z * r), (float)s.c};
+        // origin and unit are floats exactly (a float corner; a power of two)
+        const float scale = (float)g->fx_inv;
+        const float cf = __uint2float_rn((uint32_t)s.c);
+        const float cl = __int2float_rn((int32_t)(s.c - (int64_t)__float2uint_rn(cf)));
+        const float rc = __frcp_rn(cf);
+        nodes[v].g = NodeGeo{centroid_coord(s.x, s.c, cf, cl, rc, (float)g->fx_lo[0], scale),
+                             centroid_coord(s.y, s.c, cf, cl, rc, (float)g->fx_lo[1], scale),
+                             centroid_coord(s.z, s.c, cf, cl, rc, (float)g->fx_lo[2], scale),
+                             (float)s.c};
     } else {
         nodes[v].g = NodeGeo{0.f, 0.f, 0.f, 0.f};
     }
