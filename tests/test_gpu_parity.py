@@ -79,6 +79,43 @@ def test_tree_matches_oracle(name):
     g.close()
 
 
+@pytest.mark.parametrize("offset", [0.0, 4096.5])
+def test_inner_centroids_are_the_nearest_float_of_the_exact_mean(offset):
+    """Integer positions (plus a float offset) sit exactly on the fixed-point grid, so
+    each inner node's centroid has an exact rational value: offset + sum(c_i x_i) /
+    sum(c_i). The GPU's FP32 centroid must be the float nearest to it, with counts up
+    to 2^20 per neuron (node counts past 2^24, up to 2^30 at the root)."""
+    from fractions import Fraction
+    from paper_2509_26193_gb300 import relearn as R
+    rng = np.random.default_rng(77)
+    net = workloads.uniform_cube(n=1000, seed=3)
+    ix = rng.integers(0, 1024, (3, net.n))
+    ix[:, 0] = 0     # the grid's origin is a position: the frame starts at the offset
+    ix[:, 1] = 1023  # span 1023: 2^20 fixed-point units per micrometre
+    net.x, net.y, net.z = ((offset + v).astype(np.float32) for v in ix)
+    vd = rng.integers(0, 1 << 20, net.n).astype(np.int32)
+    vd[rng.random(net.n) < 0.2] = 0
+    net.vac_de = vd
+    g = GpuNet(net)
+    gt = R.relearn_get_tree(g.ctx)
+    perm = gt["perm"]
+    cnt = vd[perm].astype(object)
+    checked = 0
+    for v in np.nonzero((~gt["is_leaf"].astype(bool)) & (gt["count"] > 0))[0]:
+        sl = slice(int(gt["first"][v]), int(gt["first"][v]) + int(gt["size"][v]))
+        c = sum(cnt[sl])
+        assert c == int(gt["count"][v])
+        for a, key in enumerate(("cx", "cy", "cz")):
+            exact = Fraction(offset) + Fraction(sum(cnt[sl] * ix[a][perm][sl].astype(object)), c)
+            got = np.float32(gt[key][v])
+            near = [np.nextafter(got, np.float32(np.inf)), np.nextafter(got, np.float32(-np.inf))]
+            d = abs(Fraction(float(got)) - exact)
+            assert all(d <= abs(Fraction(float(f)) - exact) for f in near), (v, key, got, exact)
+            checked += 1
+    assert checked > 300
+    g.close()
+
+
 def _oracle_searches(net, tree, step, theta, qi=None, qe=None):
     if qi is None:
         qi, qe = oracle.queries(net.vac_ax)
