@@ -84,7 +84,7 @@ void free_all(relearn_ctx *c)
         (void **)&c->d_act_src,  (void **)&c->d_req_src,    (void **)&c->d_req_elem,
         (void **)&c->d_req_tgt,  (void **)&c->d_req_acc,    (void **)&c->d_req_prio,
         (void **)&c->d_bucket,   (void **)&c->d_tcnt,       (void **)&c->d_toff,
-        (void **)&c->d_tfill,    (void **)&c->d_newpos,     (void **)&c->d_diag_lns,
+        (void **)&c->d_newpos,   (void **)&c->d_diag_lns,
         (void **)&c->d_diag_evals, (void **)&c->d_diag_restarts, (void **)&c->d_syn_src,
         (void **)&c->d_syn_tgt,  (void **)&c->d_syn_sign,   (void **)&c->d_key,
         (void **)&c->d_key_alt,  (void **)&c->d_val,        (void **)&c->d_val_alt,
@@ -235,7 +235,6 @@ relearn_status relearn_create_batched(relearn_ctx **out, int device, int64_t max
     A(d_bucket, QC);
     A(d_tcnt, N + 1);
     A(d_toff, N + 1);
-    A(d_tfill, N + 1);
     A(d_newpos, QC + 1);
     A(d_rq_key, QC);
     A(d_rq_key_alt, QC);

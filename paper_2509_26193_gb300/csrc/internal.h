@@ -103,7 +103,7 @@ struct relearn_ctx {
     uint8_t *d_req_acc = nullptr;   // [max_searches]
     uint32_t *d_req_prio = nullptr; // [max_searches]
     uint64_t *d_bucket = nullptr;   // [max_searches] request keys grouped by target
-    int32_t *d_tcnt = nullptr, *d_toff = nullptr, *d_tfill = nullptr; // [n + 1]
+    int32_t *d_tcnt = nullptr, *d_toff = nullptr; // [n + 1]
     int32_t *d_newpos = nullptr;    // [max_searches + 1]
     uint32_t *d_rq_key = nullptr, *d_rq_key_alt = nullptr; // [max_searches] deferred restarts
     int32_t *d_rq_val = nullptr, *d_rq_val_alt = nullptr;

@@ -56,23 +56,26 @@ __device__ __forceinline__ uint64_t request_key(uint32_t prio, int64_t r)
     return ((uint64_t)prio << 32) | (uint64_t)(uint32_t)r;
 }
 
+// Each request takes a slot of its target's bucket by counting the target's count
+// down (the bucket's order does not matter: the decision ranks keys).
 __global__ void accept_scatter_kernel(const int32_t *d_Q, const int32_t *__restrict__ req_tgt,
                                       const uint32_t *__restrict__ prio,
                                       const int32_t *__restrict__ toff,
-                                      int32_t *__restrict__ tfill, uint64_t *__restrict__ bucket)
+                                      int32_t *__restrict__ tcnt, uint64_t *__restrict__ bucket)
 {
     const int64_t Q = *d_Q;
     GRID_STRIDE(r, Q)
     {
         int32_t t = req_tgt[r];
         if (t < 0) continue;
-        bucket[toff[t] + atomicAdd(&tfill[t], 1)] = request_key(prio[r], r);
+        bucket[toff[t] + atomicSub(&tcnt[t], 1) - 1] = request_key(prio[r], r);
     }
 }
 
+// A target's request count is the difference of neighbouring bucket offsets (one
+// read of two adjacent words).
 __global__ void accept_decide_kernel(const int32_t *d_Q, const int32_t *__restrict__ req_tgt,
                                      const uint32_t *__restrict__ prio,
-                                     const int32_t *__restrict__ tcnt,
                                      const int32_t *__restrict__ toff,
                                      const uint64_t *__restrict__ bucket,
                                      const int32_t *__restrict__ vac_de,
@@ -88,12 +91,12 @@ __global__ void accept_decide_kernel(const int32_t *d_Q, const int32_t *__restri
         if (t >= 0) {
             int32_t v = vac_de[t];
             if (v < 0) v = 0;
-            int32_t rt = tcnt[t];
+            const int32_t o = toff[t], rt = toff[t + 1] - o;
             if (rt <= v) {
                 a = 1;
             } else if (v > 0) {
                 const uint64_t kr = request_key(prio[r], r); // keys are distinct
-                const uint64_t *bk = bucket + toff[t];
+                const uint64_t *bk = bucket + o;
                 int32_t below = 0;
                 for (int32_t k = 0; k < rt && below < v; ++k) below += bk[k] < kr ? 1 : 0;
                 a = below < v ? 1 : 0;
@@ -422,17 +425,16 @@ cudaError_t accept_requests(relearn_ctx *c, const relearn_params &p, const int32
     const int32_t *dQ = c->d_i32 + I32_Q;
     const unsigned gq = grid_for(c->max_searches, 256, c->num_sms);
     if ((e = cudaMemsetAsync(c->d_tcnt, 0, (n + 1) * sizeof(int32_t), st))) return e;
-    if ((e = cudaMemsetAsync(c->d_tfill, 0, (n + 1) * sizeof(int32_t), st))) return e;
     if ((e = cudaMemsetAsync(c->d_i64 + I64_DECLINED, 0, sizeof(int64_t), st))) return e;
     accept_count_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_src, c->d_req_elem, c->d_req_tgt,
                                             c->d_req_prio, c->d_tcnt, p.seed, (uint32_t)p.step);
     note_launch();
     if ((e = scan_exclusive(c->d_tcnt, c->d_toff, n + 1, nullptr, nullptr, c->scan, st))) return e;
     accept_scatter_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_tgt, c->d_req_prio, c->d_toff,
-                                              c->d_tfill, c->d_bucket);
+                                              c->d_tcnt, c->d_bucket);
     note_launch();
-    accept_decide_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_tgt, c->d_req_prio, c->d_tcnt,
-                                             c->d_toff, c->d_bucket,
+    accept_decide_kernel<<<gq, 256, 0, st>>>(dQ, c->d_req_tgt, c->d_req_prio, c->d_toff,
+                                             c->d_bucket,
                                              vac_de, c->d_req_acc, c->d_newpos,
                                              c->d_i64 + I64_DECLINED);
     note_launch();
