@@ -38,7 +38,13 @@ namespace rl {
 namespace {
 
 constexpr float kTinyL = 8.673617e-19f; // 2^-60: below this S is redone with a shift
-constexpr int kUnionDepth = 4;          // sources in one cell this deep share a walk
+// Sources in one cell this deep share a walk. The forward pass cuts finer: its
+// pieces step in blocks like one union, so more pieces cost little (2^18 cube,
+// forward: depth 4 2.11 ms, 5 1.77 ms, 6 2.02 ms). The adjoint sums every piece's
+// contributions across the warp at each step, so more pieces cost a warp sum each
+// (adjoint: depth 4 5.77 ms, 5 10.8 ms, 6 31.0 ms).
+constexpr int kFwdDepth = 5, kBwdDepth = 4;
+constexpr int kLenBlock = 128; // walk steps between progress checks
 
 struct LenArgs {
     const Node *__restrict__ nodes;
@@ -239,16 +245,23 @@ __global__ void __launch_bounds__(256, kBack ? RELEARN_LEN_BWD_MIN_BLOCKS : 6)
             s.w = on_src ? (float)((double)a.vac_ax[i] * wscale) : 0.0f;
         }
         // the 32 sources (Morton order) are cut wherever two neighbours do not share a
-        // cell of depth kUnionDepth; each piece walks one union (one piece: uni)
+        // cell of depth kFwdDepth (kBwdDepth); each piece walks one union (one piece: uni)
         const int last = min(A - 1 - nb, 31);
         uint32_t code = live ? a.codes[sp] : 0u;
         code = __shfl_sync(0xffffffffu, code, live ? lane : last);
         const uint32_t nxt = __shfl_down_sync(0xffffffffu, code, 1);
         const uint32_t cuts = __ballot_sync(
-            0xffffffffu, lane < 31 && morton_common_digits(code, nxt) < kUnionDepth);
+            0xffffffffu,
+            lane < 31 && morton_common_digits(code, nxt) < (kBack ? kBwdDepth : kFwdDepth));
         const bool uni = cuts == 0;
         Fwd f;
         Bwd b;
+        // The walks step in blocks of four steps per bounds test: nodes root_end ..
+        // root_end + 2 are sentinels (no count, escape = the next node), and a piece
+        // whose walk has ended parks on root_end (its escape clamped back to it).
+        // Escapes are taken as stored; each block of kLenBlock steps must advance,
+        // which keeps a walk over a malformed tree finite.
+        int32_t p = 1, skip = on_src ? 0 : 0x7fffffff;
         if (!uni) {
             const uint32_t below = cuts & ((1u << lane) - 1u);
             const int first = below ? 32 - __clz(below) : 0;
@@ -256,18 +269,14 @@ __global__ void __launch_bounds__(256, kBack ? RELEARN_LEN_BWD_MIN_BLOCKS : 6)
             const int lastl = from ? lane + __ffs(from) - 1 : 31;
             const uint32_t gmask = (lastl == 31 ? 0xffffffffu : ((1u << (lastl + 1)) - 1u)) &
                                    ~((1u << first) - 1u);
-            int32_t p = 1, skip = on_src ? 0 : 0x7fffffff;
-            while (__any_sync(0xffffffffu, p < root_end)) {
-                const bool run = p < root_end; // uniform within the piece
-                float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-                int2 t = make_int2(p + 1, 0);
-                if (run) {
-                    load_node(&a.nodes[p], g, t); // one 256-bit read
-                }
+            auto piece_step = [&]() {
+                float4 g;
+                int2 t;
+                load_node(&a.nodes[p], g, t); // one 256-bit read
                 const float rx = __fsub_rn(s.x.x, g.x), ry = __fsub_rn(s.x.y, g.y),
                             rz = __fsub_rn(s.x.z, g.z);
                 const float D = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, __fmul_rn(rz, rz)));
-                const bool on = run && p >= skip && g.w > 0.0f;
+                const bool on = p >= skip && g.w > 0.0f;
                 const bool pass = __float_as_uint(D) + (uint32_t)t.y > thr0;
                 const bool take = on && pass && p != s.self;
                 if (on && pass) skip = t.x;
@@ -289,11 +298,20 @@ __global__ void __launch_bounds__(256, kBack ? RELEARN_LEN_BWD_MIN_BLOCKS : 6)
                     }
                 }
                 const uint32_t down = __ballot_sync(0xffffffffu, on && !pass) & gmask;
-                if (run) p = down ? p + 1 : max(t.x, p + 1);
+                p = min(down ? p + 1 : t.x, root_end);
+            };
+            while (__any_sync(0xffffffffu, p < root_end)) {
+                const int32_t p_blk = p;
+                int k = 0;
+#pragma unroll 1
+                for (; k < kLenBlock && __any_sync(0xffffffffu, p < root_end); k += 4) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) piece_step();
+                }
+                if (__any_sync(0xffffffffu, p < root_end && p <= p_blk)) break;
             }
         } else {
-            int32_t p = 1, skip = on_src ? 0 : 0x7fffffff;
-            while (p < root_end) {
+            auto uni_step = [&]() {
                 float4 g;
                 int2 t;
                 load_node(&a.nodes[p], g, t); // one 256-bit read
@@ -312,7 +330,16 @@ __global__ void __launch_bounds__(256, kBack ? RELEARN_LEN_BWD_MIN_BLOCKS : 6)
                     if (take) bwd_visit(b, s, g.w, rx, ry, rz, D, k2, two_s2, ox, oy, oz);
                     if (__any_sync(0xffffffffu, take)) add_node_warp(a.G, p, ox, oy, oz, lane);
                 }
-                p = __any_sync(0xffffffffu, on && !pass) ? p + 1 : max(t.x, p + 1);
+                p = __any_sync(0xffffffffu, on && !pass) ? p + 1 : t.x;
+            };
+            while (p < root_end) {
+                const int32_t p_blk = p;
+#pragma unroll 1
+                for (int k = 0; k < kLenBlock && p < root_end; k += 4) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) uni_step();
+                }
+                if (p <= p_blk) break;
             }
         }
         if constexpr (!kBack) {
