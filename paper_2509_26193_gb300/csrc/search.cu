@@ -64,11 +64,13 @@ constexpr float kTiny = 8.673617e-19f; // 2^-60
 constexpr int kCutSingle = 6;
 constexpr int kCutDense = 2, kCutMid = 3, kCutSparse = 4, kDenseTenths = 6, kMidTenths = 3;
 // The default also looks at how many sources the update has, per resident warp of
-// the union kernel (W = 7,296 on 152 SMs). Per-update sweeps on the 2^20-neuron
-// clustered network (ten successive updates, 907k down to 2.4k sources): with at
-// most kSplitWaves * W sources the split kernel (one warp per source) wins (61.8k
-// sources: 1.67 ms against 1.84 ms; 162k: 4.73 ms against 2.46 ms), on small trees
-// as well (4096-neuron cube, 4096 sources: 0.10 ms against 0.46 ms).
+// the union kernel (W = 9,728 on 152 SMs at 8 blocks per SM; the sweeps below were
+// taken at 6 blocks, W = 7,296, and the threshold rechecked at 8). Per-update sweeps
+// on the 2^20-neuron clustered network (ten successive updates, 907k down to 2.4k
+// sources): with at most kSplitWaves * W sources the split kernel (one warp per
+// source) wins (61.8k sources: 1.67 ms against 1.84 ms; 162k: 4.73 ms against
+// 2.46 ms), on small trees as well (4096-neuron cube, 4096 sources: 0.10 ms against
+// 0.46 ms).
 constexpr int kSplitWaves = 9;
 
 // A node of depth d is accepted iff d^2 > thr0 / 4^d, thr0 = (root length / theta)^2
