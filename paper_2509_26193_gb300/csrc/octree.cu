@@ -10,9 +10,11 @@
 // uncompressed octree. Nodes are laid out in pre-order with a skip link
 // (`escape`) per node so that a search walks the tree without a stack.
 //
-// Reduce: one thread per leaf climbs towards the root; the last child to
-// arrive at a node sums all of that node's children (in Morton order, FP64)
-// and continues upward, so every node is summed once and deterministically.
+// Reduce (bottom-up update): every node covers a contiguous Morton range, so its
+// count and count-weighted position sums are differences of one exclusive prefix
+// over the neurons in Morton order, formed in exact int64 fixed point (leaves and
+// tile sums, then each tile's prefix); each inner node then takes its two prefix
+// entries and rounds its centroid once to FP32 (see inner_sums).
 #include <mutex>
 
 #include "internal.h"
