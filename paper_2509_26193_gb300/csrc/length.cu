@@ -12,10 +12,10 @@
 //   dl_i/dx_i   = -sum_k dl_i/dc_k,   dc_k/dx_j = w_j / N_k  (w = vac_de).
 //
 // Forward: one walk of each root frontier (the search kernel's warp-union walk: the
-// warp's 32 sources, cut at the boundaries of depth-4 cells, walk one union per
-// piece),
-// FP32 attractions with Kahan-compensated sums; S, l and Dbar formed in FP64 and
-// kept per source with the exponent shift. Backward: the same walk again,
+// warp's 32 sources, cut at the boundaries of depth-5 cells, depth 4 in the adjoint,
+// walk one union per piece), FP32 attractions with Kahan-compensated sums; S, l and
+// Dbar formed in FP64 and kept per source with the exponent shift. Backward: the
+// same walk again,
 // recomputing every attraction (nothing per candidate is stored), accumulating
 // the centroid adjoints G_k = sum_i (m_i / M) dl_i/dc_k per node in FP64 and each
 // source's direct term in registers (Kahan-compensated FP32: it is a sum of terms of
